@@ -1,0 +1,161 @@
+/*
+ * opm.h - C ABI of the GB300 (sm_103a) oblique-plane deskew library.
+ *
+ * The library implements the data-parallel hot path of live OPM viewing
+ * (Lamb, Ward & Kaminski, arXiv 2211.00645): the shear deskew of a raw stack
+ * of tilted camera frames onto the real-space (z, y', x) grid and the
+ * widefield-like maximum projection of the deskewed stack, plus the adjoint
+ * of the deskew and the backward pass of the z-MIP.
+ *
+ * Geometry (lab frame, Eq. 1 with the sheet angle alpha = theta):
+ *   raw      R[n][r][x]    n in [0, nscan) scan plane, r in [0, nrows) camera
+ *                          row, x in [0, ncols) column; C order, x fastest.
+ *   output   V[k][j][x]    k in [0, nz = nrows), j in [0, ny), x in [0, nx = ncols).
+ *   n_f(j,k) = ((j - J0)*pixel - k*pixel*cos(theta)) / step
+ *   LINEAR   V = (1-w) R~[n0] + w R~[n0+1],  n0 = floor(n_f), w = n_f - n0
+ *   NEAREST  V = R~[floor(n_f + 1/2)]
+ *   R~[n] = R[n] for 0 <= n < nscan and 0 otherwise (zero-padded tent).
+ *   J0 = ceil(step/pixel) - 1,
+ *   ny = ceil(J0 + nscan*(step/pixel) + (nrows-1)*cos(theta) - 1e-9).
+ * cos(theta) is exactly 0 at 90 degrees and exactly 1/2 at 60 degrees.
+ *
+ * Conventions shared by every call below:
+ *   - Array pointers are DEVICE pointers to C-contiguous arrays owned by the
+ *     caller; the library never keeps them after the call returns.
+ *   - Compute calls are asynchronous on `cuda_stream` (a cudaStream_t; NULL is
+ *     the legacy default stream).  They neither allocate nor synchronise.
+ *   - A plan is immutable after creation and may be shared by threads and
+ *     streams.  Compute calls must run on the device the plan was created on.
+ *   - Every call returns an opm_status; on failure opm_last_error() gives a
+ *     description, valid in the calling thread until its next library call.
+ *     Output buffers are left untouched when a call fails its argument checks.
+ */
+#ifndef OPM_H
+#define OPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct opm_plan opm_plan; /* opaque; owns only its small geometry tables */
+
+typedef enum {
+  OPM_OK = 0,
+  OPM_ERR_INVALID_ARG = 1,   /* a parameter is out of its documented domain  */
+  OPM_ERR_UNSUPPORTED = 2,   /* valid but not handled (dtype pair, size)     */
+  OPM_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed            */
+  OPM_ERR_OUT_OF_MEMORY = 4, /* plan tables could not be allocated           */
+  OPM_ERR_INTERNAL = 5       /* a device-side consistency check tripped      */
+} opm_status;
+
+typedef enum { OPM_INTERP_LINEAR = 0, OPM_INTERP_NEAREST = 1 } opm_interp;
+
+typedef enum {
+  OPM_U16 = 0, /* uint16 camera counts                                      */
+  OPM_F32 = 1, /* float                                                     */
+  OPM_F64 = 2  /* double (gradient checks only)                             */
+} opm_dtype;
+
+/*
+ * opm_plan_create - geometry of one acquisition (Eq. 1; Fig. 2c remap).
+ *   nscan >= 2 scan planes, nrows >= 1 camera rows, ncols >= 1 columns,
+ *   theta_deg in (0, 90] sheet angle to the scan axis, step > 0 scan step,
+ *   pixel > 0 sample-plane pixel size (step and pixel in the same unit),
+ *   interp LINEAR or NEAREST.  On success *out receives a new plan.
+ * Derives nz, ny, J0 in FP64 and splits the per-column term (j-J0)*pixel/step
+ * and the per-row term k*cos(theta)*pixel/step into an integer and an FP32
+ * fraction, uploaded to the current CUDA device (the plan's device) when one
+ * is present.  A plan made without a device answers opm_plan_shape but its
+ * compute calls return OPM_ERR_CUDA.
+ * Errors: OPM_ERR_INVALID_ARG (domain, NULL out), OPM_ERR_UNSUPPORTED (a
+ * dimension of the output grid above 2^31 - 1 or more than 2^40 voxels),
+ * OPM_ERR_OUT_OF_MEMORY, OPM_ERR_CUDA.
+ */
+opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
+                           double theta_deg, double step, double pixel,
+                           opm_interp interp, opm_plan** out);
+
+/* Output grid of a plan: nz = nrows, ny, nx = ncols, and J0.  Any output
+ * pointer may be NULL.  Errors: OPM_ERR_INVALID_ARG for a NULL plan. */
+opm_status opm_plan_shape(const opm_plan* plan, int64_t* nz, int64_t* ny,
+                          int64_t* nx, int64_t* j0);
+
+/* Frees a plan and its device tables.  NULL is accepted.  The caller must not
+ * destroy a plan while work that uses it is still queued on a stream. */
+opm_status opm_plan_destroy(opm_plan* plan);
+
+/*
+ * opm_deskew - materialise the deskewed volume (Fig. 2c).
+ *   raw  [nscan][nrows][ncols] of in_t;  vol [nz][ny][nx] of out_t.
+ *   Supported (in_t -> out_t): U16->F32, U16->U16, F32->F32, F32->U16,
+ *   F64->F64.  A U16 output is the value rounded half to even and clamped to
+ *   [0, 65535].
+ * Errors: OPM_ERR_INVALID_ARG (NULL plan or pointers), OPM_ERR_UNSUPPORTED
+ * (dtype pair), OPM_ERR_CUDA (launch failure, wrong device).
+ */
+opm_status opm_deskew(const opm_plan* plan, const void* raw, opm_dtype in_t,
+                      void* vol, opm_dtype out_t, void* cuda_stream);
+
+/*
+ * opm_project - widefield-like live view, fused with the deskew (Fig. 2d):
+ * the volume is never written to memory.
+ *   raw  [nscan][nrows][ncols] of in_t (U16 or F32)
+ *   zmip [ny][nx] float  max over k of V          (the widefield-like view)
+ *   zsum [ny][nx] float  sum over k of V
+ *   ymip [nz][nx] float  max over j of V          (side view)
+ *   argz [ny][nx] int32  smallest k attaining zmip (needed by opm_mip_backward)
+ * Any of the four outputs may be NULL, but not all of them.  The maxima run
+ * over the whole output grid, zero-padded voxels included.
+ * Errors: OPM_ERR_INVALID_ARG (NULL plan/raw, all outputs NULL),
+ * OPM_ERR_UNSUPPORTED (in_t F64), OPM_ERR_CUDA.
+ */
+opm_status opm_project(const opm_plan* plan, const void* raw, opm_dtype in_t,
+                       float* zmip, float* zsum, float* ymip, int32_t* argz,
+                       void* cuda_stream);
+
+/*
+ * opm_skew_adjoint - transpose of the LINEAR deskew map:
+ *   raw_out[n][k][x] = sum_j vol[k][j][x] * t(n_f(j,k) - n),  t(u) = max(0, 1-|u|).
+ *   vol [nz][ny][nx] and raw_out [nscan][nrows][ncols], both of type t (F32 or
+ *   F64).  Each output element is a gather over j in ascending order: no
+ *   atomics, bitwise reproducible.  Plans made with NEAREST use the matching
+ *   0/1 weights.
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED (t = U16), OPM_ERR_CUDA.
+ */
+opm_status opm_skew_adjoint(const opm_plan* plan, const void* vol,
+                            void* raw_out, opm_dtype t, void* cuda_stream);
+
+/*
+ * opm_mip_backward - gradient of sum(g_zmip * zmip) with respect to the raw
+ * stack, routed through the voxel that attained each maximum:
+ *   g_raw[n][k][x] = sum_j [argz[j][x] == k] g_zmip[j][x] t(n_f(j,k) - n).
+ *   g_zmip [ny][nx] float, argz [ny][nx] int32 (from opm_project),
+ *   g_raw [nscan][nrows][ncols] float (fully overwritten).
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_CUDA.
+ */
+opm_status opm_mip_backward(const opm_plan* plan, const float* g_zmip,
+                            const int32_t* argz, float* g_raw,
+                            void* cuda_stream);
+
+/*
+ * opm_plan_check - synchronising diagnostic (not for the hot path): waits for
+ * the plan's device, then reports OPM_ERR_INTERNAL if any kernel launched with
+ * this plan recorded a failed internal consistency check (and clears the
+ * record), OPM_OK otherwise.
+ */
+opm_status opm_plan_check(const opm_plan* plan);
+
+/* Description of the last failure in the calling thread ("" if none). */
+const char* opm_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int opm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPM_H */

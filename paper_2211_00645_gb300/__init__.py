@@ -1,0 +1,249 @@
+"""Python binding of libopm.so, the sm_103a OPM deskew library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/opm.h``.  PyTorch provides
+device memory and streams.  The functions ``opm_*`` mirror the C entry points
+one to one (tensors in place of pointers, the current torch stream by
+default); ``deskew``/``project``/``skew_adjoint``/``mip_backward`` allocate
+their outputs with torch and call them.
+
+There is no CPU fallback: if the library has not been built, or no CUDA device
+is present, these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libopm.so")
+
+OPM_OK, OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED, OPM_ERR_CUDA, OPM_ERR_OUT_OF_MEMORY, OPM_ERR_INTERNAL = range(6)
+OPM_INTERP_LINEAR, OPM_INTERP_NEAREST = 0, 1
+OPM_U16, OPM_F32, OPM_F64 = 0, 1, 2
+
+_STATUS = {
+    OPM_ERR_INVALID_ARG: "OPM_ERR_INVALID_ARG",
+    OPM_ERR_UNSUPPORTED: "OPM_ERR_UNSUPPORTED",
+    OPM_ERR_CUDA: "OPM_ERR_CUDA",
+    OPM_ERR_OUT_OF_MEMORY: "OPM_ERR_OUT_OF_MEMORY",
+    OPM_ERR_INTERNAL: "OPM_ERR_INTERNAL",
+}
+
+# Every symbol the header declares, with its ctypes signature.
+_SIGS = {
+    "opm_plan_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "opm_plan_shape": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4),
+    "opm_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "opm_deskew": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_int, ctypes.c_void_p]),
+    "opm_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
+    "opm_skew_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p]),
+    "opm_mip_backward": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "opm_plan_check": (ctypes.c_int, [ctypes.c_void_p]),
+    "opm_last_error": (ctypes.c_char_p, []),
+    "opm_version": (ctypes.c_int, []),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+class OpmError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        super().__init__(f"{func}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libopm.so (built by ``paper_2211_00645_gb300.build``) once."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, func: str):
+    if status != OPM_OK:
+        raise OpmError(status, func, load().opm_last_error().decode(errors="replace"))
+
+
+class Plan:
+    """Owns an ``opm_plan*``; destroyed with the object."""
+
+    def __init__(self, nscan, nrows, ncols, theta_deg, step, pixel, interp=OPM_INTERP_LINEAR):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.opm_plan_create(int(nscan), int(nrows), int(ncols), float(theta_deg), float(step),
+                                   float(pixel), int(interp), ctypes.byref(h)), "opm_plan_create")
+        self._h = h
+        self.nscan, self.nrows, self.ncols = int(nscan), int(nrows), int(ncols)
+        self.theta_deg, self.step, self.pixel, self.interp = float(theta_deg), float(step), float(pixel), int(interp)
+        self.nz, self.ny, self.nx, self.J0 = opm_plan_shape(self)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def raw_shape(self):
+        return (self.nscan, self.nrows, self.ncols)
+
+    @property
+    def vol_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load().opm_plan_destroy(self._h), "opm_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def opm_plan_create(nscan, nrows, ncols, theta_deg, step, pixel, interp=OPM_INTERP_LINEAR) -> Plan:
+    return Plan(nscan, nrows, ncols, theta_deg, step, pixel, interp)
+
+
+def opm_plan_shape(plan: Plan):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(load().opm_plan_shape(plan.handle, *[ctypes.byref(x) for x in v]), "opm_plan_shape")
+    return tuple(int(x.value) for x in v)
+
+
+def opm_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def opm_plan_check(plan: Plan):
+    _check(load().opm_plan_check(plan.handle), "opm_plan_check")
+
+
+# ------------------------------------------------------------------ tensors
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.uint16: OPM_U16, torch.float32: OPM_F32, torch.float64: OPM_F64}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype} (uint16, float32 or float64)")
+    return m[t.dtype]
+
+
+def _ptr(t, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def opm_deskew(plan: Plan, raw, vol, stream=None):
+    _check(load().opm_deskew(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
+                             _ptr(vol, plan.vol_shape, "vol"), _dtype_code(vol), _stream(stream)), "opm_deskew")
+
+
+def opm_project(plan: Plan, raw, zmip=None, zsum=None, ymip=None, argz=None, stream=None):
+    torch = _torch()
+    for t, nm in ((zmip, "zmip"), (zsum, "zsum"), (ymip, "ymip")):
+        if t is not None and t.dtype != torch.float32:
+            raise TypeError(f"{nm} must be float32")
+    if argz is not None and argz.dtype != torch.int32:
+        raise TypeError("argz must be int32")
+    pj = (plan.ny, plan.nx)
+    _check(load().opm_project(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
+                              _ptr(zmip, pj, "zmip"), _ptr(zsum, pj, "zsum"),
+                              _ptr(ymip, (plan.nz, plan.nx), "ymip"), _ptr(argz, pj, "argz"),
+                              _stream(stream)), "opm_project")
+
+
+def opm_skew_adjoint(plan: Plan, vol, raw_out, stream=None):
+    if vol.dtype != raw_out.dtype:
+        raise TypeError("vol and raw_out must share a dtype")
+    _check(load().opm_skew_adjoint(plan.handle, _ptr(vol, plan.vol_shape, "vol"),
+                                   _ptr(raw_out, plan.raw_shape, "raw_out"), _dtype_code(vol),
+                                   _stream(stream)), "opm_skew_adjoint")
+
+
+def opm_mip_backward(plan: Plan, g_zmip, argz, g_raw, stream=None):
+    torch = _torch()
+    if g_zmip.dtype != torch.float32 or g_raw.dtype != torch.float32 or argz.dtype != torch.int32:
+        raise TypeError("g_zmip/g_raw must be float32 and argz int32")
+    pj = (plan.ny, plan.nx)
+    _check(load().opm_mip_backward(plan.handle, _ptr(g_zmip, pj, "g_zmip"), _ptr(argz, pj, "argz"),
+                                   _ptr(g_raw, plan.raw_shape, "g_raw"), _stream(stream)), "opm_mip_backward")
+
+
+# ------------------------------------------------------- allocating helpers
+def deskew(plan: Plan, raw, out_dtype=None, stream=None):
+    torch = _torch()
+    if out_dtype is None:
+        out_dtype = torch.float64 if raw.dtype == torch.float64 else torch.float32
+    vol = torch.empty(plan.vol_shape, dtype=out_dtype, device=raw.device)
+    opm_deskew(plan, raw, vol, stream)
+    return vol
+
+
+def project(plan: Plan, raw, zmip=True, zsum=False, ymip=False, argz=False, stream=None):
+    """Returns a dict with the requested projections."""
+    torch = _torch()
+    dev = raw.device
+    out = {}
+    if zmip:
+        out["zmip"] = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
+    if zsum:
+        out["zsum"] = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
+    if ymip:
+        out["ymip"] = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
+    if argz:
+        out["argz"] = torch.empty((plan.ny, plan.nx), dtype=torch.int32, device=dev)
+    opm_project(plan, raw, out.get("zmip"), out.get("zsum"), out.get("ymip"), out.get("argz"), stream)
+    return out
+
+
+def skew_adjoint(plan: Plan, vol, stream=None):
+    torch = _torch()
+    raw = torch.empty(plan.raw_shape, dtype=vol.dtype, device=vol.device)
+    opm_skew_adjoint(plan, vol, raw, stream)
+    return raw
+
+
+def mip_backward(plan: Plan, g_zmip, argz, stream=None):
+    torch = _torch()
+    g = torch.empty(plan.raw_shape, dtype=torch.float32, device=g_zmip.device)
+    opm_mip_backward(plan, g_zmip, argz, g, stream)
+    return g

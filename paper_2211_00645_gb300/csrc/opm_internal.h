@@ -1,0 +1,97 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "opm.h"
+
+namespace opm {
+
+// An FP64 coordinate split into floor (int32) and an FP32 fraction.  The
+// per-voxel plane coordinate n_f(j,k) = A_j - B_k is rebuilt on the GPU as
+// (A.i - B.i) + (A.f - B.f): the integer part is exact and the fraction keeps
+// ~1e-7 absolute error, where a plain FP32 product j*rho would lose ~1e-4 at
+// j ~ 2500 (enough to move a uint16 voxel by several counts).
+struct Split {
+  int32_t i;
+  float f;
+};
+
+// Row band of one 32-column j-tile: rows [lo, hi) may carry non-zero weight,
+// every row outside it is structurally zero for all columns of the tile.
+struct Band {
+  int32_t lo;
+  int32_t hi;
+};
+
+constexpr int kTileJ = 32;  // j-columns per CTA tile of the projection kernels
+
+// Error bits recorded by kernels in the plan's device error word.
+enum : unsigned {
+  kErrSlabRange = 1u,   // a plane offset fell outside the staged slab
+  kErrWaitTimeout = 2u, // an mbarrier wait gave up
+};
+
+void set_error(const std::string& msg);
+opm_status fail(opm_status s, const std::string& msg);
+opm_status cuda_fail(cudaError_t e, const char* what);
+
+// Device-side view of a plan, passed by value to kernels.
+struct PlanView {
+  const Split* A;     // [ny]  (j - J0) * pixel/step (+1/2 for NEAREST)
+  const Split* B;     // [nz]  k * cos(theta) * pixel/step
+  const Band* band;   // [ceil(ny / kTileJ)]
+  const float* yinit; // [nz]  0 if row k has a structurally zero voxel, else -inf
+  unsigned* err;      // error word
+  int nscan, nrows, ncols, nz, ny, nx, J0;
+  int linear;         // 1 LINEAR, 0 NEAREST
+  float rinv;         // step / pixel (float), used only to size search windows
+};
+
+}  // namespace opm
+
+struct opm_plan {
+  int64_t nscan, nrows, ncols, nz, ny, nx, J0;
+  double theta, step, pixel, c, rho;
+  int interp;
+  int force_generic;  // use the plain (non-TMA) kernels for every call
+  std::vector<opm::Split> hA, hB;
+  std::vector<opm::Band> hBand;
+  std::vector<float> hYinit;
+  int device;        // -1: created without a device
+  void* dmem;        // one allocation holding every device table
+  opm::PlanView view;
+};
+
+namespace opm {
+
+// Kernel launchers (one per translation unit).  Each returns OPM_OK or an
+// error already recorded with fail()/cuda_fail().
+opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t,
+                          float* zmip, float* zsum, float* ymip, int32_t* argz,
+                          cudaStream_t s);
+opm_status launch_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
+                         void* vol, opm_dtype out_t, cudaStream_t s);
+opm_status launch_adjoint(const opm_plan* p, const void* vol, void* raw_out,
+                          opm_dtype t, cudaStream_t s);
+opm_status launch_mip_backward(const opm_plan* p, const float* g,
+                               const int32_t* argz, float* g_raw,
+                               cudaStream_t s);
+
+// Device-side helpers shared by the kernels -------------------------------
+#ifdef __CUDACC__
+// Lower plane n0 and weight w of output (j, k): n_f = (A.i - B.i) + (A.f - B.f).
+__device__ __forceinline__ void plane_weight(Split a, Split b, int linear,
+                                             int& n0, float& w) {
+  const float d = a.f - b.f;  // in [-1, 1]
+  const int neg = d < 0.0f;
+  n0 = a.i - b.i - neg;
+  w = linear ? (neg ? d + 1.0f : d) : 0.0f;
+}
+#endif
+
+}  // namespace opm

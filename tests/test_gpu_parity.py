@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+identical seeded inputs.  Bound: max |gpu - oracle| <= 1e-4 * max |oracle| per
+FP32 output array, rounded uint16 outputs within 1 LSB, argmax pointing at a
+maximal voxel (and at the oracle's first one wherever the maximum is clear).
+"""
+import numpy as np
+import pytest
+
+import opm_synth
+import oracle as O
+from gpu_util import TOL, assert_between, assert_close, check_argz, nearest_bounds, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# (nscan, nrows, ncols, theta, step, pixel): tiles, ragged tails, exact-cos
+# angles, step < pixel, odd column counts (no TMA), single row/column.
+SHAPES = [
+    (64, 128, 128, 30.0, 0.4, 0.115),     # the oracle-sized workload
+    (40, 70, 264, 35.0, 0.3, 0.1),        # ragged x tile (264 = 256 + 8), ny % 32 != 0
+    (33, 50, 200, 45.0, 0.2, 0.115),
+    (12, 30, 40, 90.0, 0.125, 0.125),     # pure transpose
+    (10, 24, 48, 60.0, 0.125, 0.125),     # weights in {0, 1/2}
+    (16, 20, 64, 35.0, 0.05, 0.1),        # step < pixel: two planes per column step
+    (9, 17, 37, 30.0, 0.4, 0.115),        # odd column count: plain kernels
+    (2, 1, 1, 90.0, 0.2, 0.1),
+    (2, 3, 9, 30.0, 0.4, 0.115),
+    (5, 1, 8, 20.0, 0.7, 0.1),
+]
+
+
+def _stack(shape, seed=3, blobs=12):
+    n, r, c = shape[:3]
+    cfg = opm_synth.StackConfig("t", n, r, c, *shape[3:], n_blobs=blobs, sigma=(1.0, 3.0),
+                                amp=(200.0, 4000.0), seed=seed)
+    return opm_synth.raw_stack(cfg)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("interp", [0, 1])
+def test_deskew_u16_to_f32(lib, shape, interp):
+    R = _stack(shape)
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape, interp=interp)
+    vol = lib.deskew(plan, to_dev(R, torch))
+    torch.cuda.synchronize()
+    if interp == O.NEAREST:
+        lo, hi = nearest_bounds(R, g, O)
+        assert_between(vol.cpu().numpy(), lo, hi, what=f"deskew nearest {shape}")
+    else:
+        V = O.deskew(R.astype(np.float64), g, interp)
+        assert_close(vol.cpu().numpy(), V, what=f"deskew {shape}")
+    lib.opm_plan_check(plan)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:6])
+def test_deskew_u16_rounded(lib, shape):
+    R = _stack(shape)
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape)
+    vol = lib.deskew(plan, to_dev(R, torch), out_dtype=torch.uint16)
+    torch.cuda.synchronize()
+    ref = O.to_u16(O.deskew(R.astype(np.float64), g)).astype(np.int64)
+    got = vol.cpu().to(torch.int32).numpy().astype(np.int64)
+    assert np.max(np.abs(got - ref)) <= 1
+
+
+@pytest.mark.parametrize("shape", SHAPES[:7])
+def test_deskew_f32_signed(lib, shape):
+    x = opm_synth.gaussian(shape[:3], 5, np.float32)
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape)
+    vol = lib.deskew(plan, to_dev(x, torch))
+    torch.cuda.synchronize()
+    assert_close(vol.cpu().numpy(), O.deskew(x.astype(np.float64), g), what="deskew f32")
+
+
+@pytest.mark.parametrize("shape", [SHAPES[1], SHAPES[5], SHAPES[6]])
+def test_deskew_f64(lib, shape):
+    x = opm_synth.gaussian(shape[:3], 6, np.float64)
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape)
+    vol = lib.deskew(plan, to_dev(x, torch))
+    torch.cuda.synchronize()
+    # weights carry the FP32 fraction of the split tables (~6e-8)
+    assert_close(vol.cpu().numpy(), O.deskew(x, g), tol=1e-6, what="deskew f64")
+
+
+def test_theta60_bitwise(lib):
+    """Weights are exactly 0 or 1/2: the FP32 result equals the oracle rounded to FP32."""
+    shape = (10, 24, 48, 60.0, 0.125, 0.125)
+    R = _stack(shape)
+    plan = lib.Plan(*shape)
+    vol = lib.deskew(plan, to_dev(R, torch)).cpu().numpy()
+    ref = O.deskew(R.astype(np.float64), O.geometry(*shape)).astype(np.float32)
+    assert np.array_equal(vol, ref)
+
+
+def test_bright_voxel_position(lib):
+    shape = (64, 128, 16, 30.0, 0.4, 0.115)
+    R = opm_synth.bright_voxel(shape[:3], 20, 70, 5, 1000.0, np.float64).astype(np.uint16)
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape)
+    vol = lib.deskew(plan, to_dev(R, torch)).cpu().numpy()
+    nzk, nzj, nzx = np.nonzero(vol)
+    assert set(nzk) == {70} and set(nzx) == {5}
+    jstar = g.J0 + (20 * g.step + 70 * g.pixel * g.c) / g.pixel
+    assert abs(int(np.argmax(vol[70, :, 5])) - round(jstar)) <= 1
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("interp", [0, 1])
+def test_project_u16_all_outputs(lib, shape, interp):
+    R = _stack(shape)
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape, interp=interp)
+    out = lib.project(plan, to_dev(R, torch), zmip=True, zsum=True, ymip=True, argz=True)
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    Rf = R.astype(np.float64)
+    if interp == O.NEAREST:
+        lo, hi = nearest_bounds(R, g, O)
+        assert_between(out["zmip"].cpu().numpy(), lo.max(0), hi.max(0), what="zmip nearest")
+        assert_between(out["zsum"].cpu().numpy(), lo.sum(0), hi.sum(0), what="zsum nearest")
+        assert_between(out["ymip"].cpu().numpy(), lo.max(1), hi.max(1), what="ymip nearest")
+        a = out["argz"].cpu().numpy().astype(np.int64)
+        picked = np.take_along_axis(hi, a[None], axis=0)[0]
+        assert np.all(picked >= lo.max(0) - TOL * max(np.max(hi), 1e-30))
+        return
+    zmip, zsum, ymip, argz = O.project(Rf, g, interp)
+    assert_close(out["zmip"].cpu().numpy(), zmip, what="zmip")
+    assert_close(out["zsum"].cpu().numpy(), zsum, what="zsum")
+    assert_close(out["ymip"].cpu().numpy(), ymip, what="ymip")
+    V = O.deskew(Rf, g, interp)
+    check_argz(out["argz"].cpu().numpy(), V, zmip, TOL * max(np.max(np.abs(zmip)), 1e-30))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_project_u16_fast_path(lib, shape):
+    """z-MIP and y-MIP only: the two-row, chunked variant."""
+    R = _stack(shape, seed=4)
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape)
+    raw = to_dev(R, torch)
+    for want in ({"zmip": True, "ymip": True}, {"zmip": True}, {"ymip": True, "zmip": False}):
+        out = lib.project(plan, raw, **want)
+        torch.cuda.synchronize()
+        zmip, _, ymip, _ = O.project(R.astype(np.float64), g)
+        if "zmip" in out:
+            assert_close(out["zmip"].cpu().numpy(), zmip, what=f"zmip {want}")
+        if "ymip" in out:
+            assert_close(out["ymip"].cpu().numpy(), ymip, what=f"ymip {want}")
+    lib.opm_plan_check(plan)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:7])
+def test_project_f32_signed(lib, shape):
+    """Negative inputs: zero-padded voxels must still take part in the maxima."""
+    x = opm_synth.gaussian(shape[:3], 8, np.float32) - 2.0
+    g = O.geometry(*shape)
+    plan = lib.Plan(*shape)
+    out = lib.project(plan, to_dev(x, torch), zmip=True, zsum=True, ymip=True, argz=True)
+    torch.cuda.synchronize()
+    xf = x.astype(np.float64)
+    zmip, zsum, ymip, argz = O.project(xf, g)
+    assert_close(out["zmip"].cpu().numpy(), zmip, what="zmip f32")
+    assert_close(out["zsum"].cpu().numpy(), zsum, what="zsum f32")
+    assert_close(out["ymip"].cpu().numpy(), ymip, what="ymip f32")
+    V = O.deskew(xf, g)
+    check_argz(out["argz"].cpu().numpy(), V, zmip, TOL * np.max(np.abs(zmip)))
+
+
+def test_project_matches_reduced_deskew_bitwise(lib):
+    """The fused projections reduce exactly the FP32 voxels opm_deskew writes."""
+    shape = SHAPES[1]
+    R = _stack(shape)
+    plan = lib.Plan(*shape)
+    raw = to_dev(R, torch)
+    vol = lib.deskew(plan, raw)
+    fast = lib.project(plan, raw, zmip=True, ymip=True)
+    full = lib.project(plan, raw, zmip=True, ymip=True, argz=True)
+    torch.cuda.synchronize()
+    zref = vol.max(dim=0).values
+    yref = vol.max(dim=1).values
+    assert torch.equal(fast["zmip"], zref) and torch.equal(fast["ymip"], yref)
+    assert torch.equal(full["zmip"], zref) and torch.equal(full["ymip"], yref)
+
+
+def test_plain_kernels_match_tma(lib, monkeypatch):
+    """OPM_FORCE_GENERIC selects the plain kernels; both paths agree."""
+    shape = SHAPES[1]
+    R = _stack(shape)
+    raw = to_dev(R, torch)
+    tma = lib.project(lib.Plan(*shape), raw, zmip=True, zsum=True, ymip=True, argz=True)
+    monkeypatch.setenv("OPM_FORCE_GENERIC", "1")
+    plain_plan = lib.Plan(*shape)
+    monkeypatch.delenv("OPM_FORCE_GENERIC")
+    plain = lib.project(plain_plan, raw, zmip=True, zsum=True, ymip=True, argz=True)
+    torch.cuda.synchronize()
+    for k in ("zmip", "ymip"):
+        assert torch.equal(tma[k], plain[k]), k
+    assert rel_err(tma["zsum"].cpu().numpy(), plain["zsum"].cpu().numpy()) < 1e-6
+    assert torch.equal(tma["argz"], plain["argz"])
+
+
+@pytest.mark.parametrize("shape", SHAPES[:7])
+def test_adjoint_f32(lib, shape):
+    g = O.geometry(*shape)
+    y = opm_synth.gaussian((g.nz, g.ny, g.nx), 9, np.float32)
+    plan = lib.Plan(*shape)
+    G = lib.skew_adjoint(plan, to_dev(y, torch))
+    torch.cuda.synchronize()
+    assert_close(G.cpu().numpy(), O.skew_adjoint(y.astype(np.float64), g), what="adjoint")
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[5], SHAPES[6]])
+def test_adjoint_f64(lib, shape):
+    g = O.geometry(*shape)
+    y = opm_synth.gaussian((g.nz, g.ny, g.nx), 10, np.float64)
+    plan = lib.Plan(*shape)
+    G = lib.skew_adjoint(plan, to_dev(y, torch))
+    torch.cuda.synchronize()
+    assert_close(G.cpu().numpy(), O.skew_adjoint(y, g), tol=1e-6, what="adjoint f64")
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[2], SHAPES[5]])
+def test_dot_test_fp32(lib, shape):
+    """<A x, y> = <x, A^T y> to 1e-6 relative with the FP32 kernels."""
+    g = O.geometry(*shape)
+    x = opm_synth.gaussian(shape[:3], 11, np.float32)
+    y = opm_synth.gaussian((g.nz, g.ny, g.nx), 12, np.float32)
+    plan = lib.Plan(*shape)
+    Ax = lib.deskew(plan, to_dev(x, torch)).double()
+    Aty = lib.skew_adjoint(plan, to_dev(y, torch)).double()
+    lhs = float((Ax * to_dev(y, torch).double()).sum())
+    rhs = float((to_dev(x, torch).double() * Aty).sum())
+    scale = float(Ax.norm() * to_dev(y, torch).double().norm())
+    assert abs(lhs - rhs) <= 1e-6 * scale
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1], SHAPES[6]])
+def test_mip_backward(lib, shape):
+    g = O.geometry(*shape)
+    x = opm_synth.gaussian(shape[:3], 13, np.float32)   # continuous: no ties
+    gz = opm_synth.gaussian((g.ny, g.nx), 14, np.float32)
+    plan = lib.Plan(*shape)
+    out = lib.project(plan, to_dev(x, torch), zmip=True, argz=True)
+    torch.cuda.synchronize()
+    zmip, _, _, argz = O.project(x.astype(np.float64), g)
+    a_gpu = out["argz"].cpu().numpy()
+    agree = a_gpu == argz
+    assert agree.mean() > 0.999
+    G = lib.mip_backward(plan, to_dev(gz, torch), to_dev(argz.astype(np.int32), torch))
+    torch.cuda.synchronize()
+    assert_close(G.cpu().numpy(), O.mip_backward(gz.astype(np.float64), argz, g), what="mip backward")
+
+
+def test_non_default_stream_and_no_allocation(lib):
+    shape = SHAPES[0]
+    R = _stack(shape)
+    plan = lib.Plan(*shape)
+    raw = to_dev(R, torch)
+    zmip = torch.empty((plan.ny, plan.nx), device="cuda")
+    ymip = torch.empty((plan.nz, plan.nx), device="cuda")
+    vol = torch.empty(plan.vol_shape, device="cuda")
+    s = torch.cuda.Stream()
+    # warm-up: the first launch of each kernel loads its module
+    lib.opm_project(plan, raw, zmip, None, ymip, None)
+    lib.opm_deskew(plan, raw, vol)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            lib.opm_project(plan, raw, zmip, None, ymip, None, stream=s)
+            lib.opm_deskew(plan, raw, vol, stream=s)
+    s.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    zref, _, yref, _ = O.project(R.astype(np.float64), O.geometry(*shape))
+    assert_close(zmip.cpu().numpy(), zref)
+    assert_close(ymip.cpu().numpy(), yref)
+
+
+def test_abi_errors_on_device(lib):
+    plan = lib.Plan(8, 6, 16, 30.0, 0.4, 0.115)
+    raw = torch.zeros(plan.raw_shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.OpmError) as e:
+        lib.project(plan, raw)
+    assert e.value.status == lib.OPM_ERR_UNSUPPORTED
+    vol = torch.zeros(plan.vol_shape, dtype=torch.float32, device="cuda")
+    with pytest.raises(lib.OpmError) as e:
+        lib.opm_deskew(plan, raw, vol)
+    assert e.value.status == lib.OPM_ERR_UNSUPPORTED
+    raw16 = torch.zeros(plan.raw_shape, dtype=torch.uint16, device="cuda")
+    st = lib.load().opm_project(plan.handle, __import__("ctypes").c_void_p(raw16.data_ptr()), lib.OPM_U16,
+                                None, None, None, None, None)
+    assert st == lib.OPM_ERR_INVALID_ARG
+
+
+@pytest.fixture(scope="module")
+def liveview():
+    c = opm_synth.CONFIGS["liveview_200x512x2048"]
+    return c, opm_synth.raw_stack(c)
+
+
+def test_liveview_full_size_sampled(lib, liveview):
+    """200x512x2048 live-view stack in the bench's launch configuration:
+    every z-MIP/y-MIP pixel of seeded sample columns and all tile edges."""
+    c, R = liveview
+    g = O.geometry(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    plan = lib.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    raw = to_dev(R, torch)
+    out = lib.project(plan, raw, zmip=True, ymip=True)
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    zg = out["zmip"].cpu().numpy()
+    yg = out["ymip"].cpu().numpy()
+    rng = np.random.default_rng(2)
+    xs = np.unique(np.concatenate([rng.integers(0, c.ncols, 24), [0, 255, 256, 1023, 1024, c.ncols - 1]]))
+    Rs = R[:, :, xs].astype(np.float64)       # x columns are independent
+    gs = O.geometry(c.nscan, c.nrows, len(xs), c.theta_deg, c.step, c.pixel)
+    zmip, _, ymip, _ = O.project(Rs, gs)
+    assert_close(zg[:, xs], zmip, what="zmip sampled")
+    assert_close(yg[:, xs], ymip, what="ymip sampled")
+    # every column: the fused projection equals a second path (plain kernels)
+    vol = lib.deskew(plan, raw)
+    torch.cuda.synchronize()
+    assert torch.equal(vol.max(dim=0).values, out["zmip"])
+    assert torch.equal(vol.max(dim=1).values, out["ymip"])
+    del vol
+    # full FP32 volume on sampled voxels
+    ks = rng.integers(0, g.nz, 2000)
+    js = rng.integers(0, g.ny, 2000)
+    xv = rng.integers(0, g.nx, 2000)
+    vol = lib.deskew(plan, raw)
+    torch.cuda.synchronize()
+    got = vol[torch.from_numpy(ks).cuda(), torch.from_numpy(js).cuda(), torch.from_numpy(xv).cuda()].cpu().numpy()
+    ref = O.voxels(R, g, ks, js, xv)
+    assert np.max(np.abs(got - ref)) <= TOL * float(np.max(np.abs(zmip)))

@@ -109,19 +109,12 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def run_reference(args):
     """The FP64 oracle timed on the host cores, per step on a bounded sample."""
     import oracle as O
 
-    ws, rank, _ = dist_env()
-    if rank != 0:
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     cfg = opm_synth.CONFIGS[WORKLOAD]
     Rfull = opm_synth.raw_stack(cfg)
@@ -197,8 +190,9 @@ def main():
     import torch
     import paper_2211_00645_gb300 as opm
     from paper_2211_00645_gb300 import build as opm_build
+    from paper_2211_00645_gb300 import dist as pdist
 
-    ws, rank, local = dist_env()
+    ws, rank, local = pdist.env()
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -237,8 +231,7 @@ def main():
     sampler = ClockSampler(torch.cuda.current_device())
     if rank == 0:
         sampler.start()
-    if ws > 1:
-        dist.barrier()
+    pdist.barrier()
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
@@ -255,18 +248,13 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     t_live = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(K)) * 1e-3
     t_vol = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(K)) * 1e-3
-    ms_step = total_ms / K
-    if ws > 1:
-        tt = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = pdist.max_over_ranks(total_ms / K, device=dev)
     opm.opm_plan_check(plan)
 
     # ---- end to end through the C ABI: pinned host raw in, live view out
     E = max(10, K // 10)
     torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
+    pdist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -277,11 +265,7 @@ def main():
         host_y.copy_(ymip, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / E
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = pdist.max_over_ranks(e0.elapsed_time(e1) / E, device=dev)
 
     if rank != 0:
         dist.destroy_process_group()

@@ -59,6 +59,8 @@ struct opm_plan {
   double theta, step, pixel, c, rho;
   int interp;
   int force_generic;  // use the plain (non-TMA) kernels for every call
+  int P;              // planes staged per row for a 32-column tile
+  int fast_ok;        // full tiles never step more than one plane per column
   std::vector<opm::Split> hA, hB;
   std::vector<opm::Band> hBand;
   std::vector<float> hYinit;

@@ -155,6 +155,26 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
       p->hBand[t] = Band{(int32_t)lo, (int32_t)hi};
     }
 
+    // Slab depth of a 32-column tile, and whether the fast projection kernel
+    // may assume that, within every full tile, consecutive columns sit on the
+    // same or the next plane and the tile spans at most P - 1 planes.  The
+    // check replays the kernels' own IEEE single-precision plane formula.
+    const double Pd = std::floor((kTileJ - 1) * p->rho) + 4.0;
+    p->P = Pd > 256.0 ? 257 : (int)Pd;
+    p->fast_ok = (p->rho <= 1.0 && p->P <= 256) ? 1 : 0;
+    for (int64_t t = 0; p->fast_ok && (t + 1) * kTileJ <= ny; ++t) {
+      for (int64_t k = 0; p->fast_ok && k < nrows; ++k) {
+        const int base = host_n0(p->hA[t * kTileJ], p->hB[k]);
+        int prev = base;
+        for (int l = 1; l < kTileJ; ++l) {
+          const int n0 = host_n0(p->hA[t * kTileJ + l], p->hB[k]);
+          if ((l % 8) != 0 && n0 != prev && n0 != prev + 1) p->fast_ok = 0;
+          if (n0 - base > p->P - 2 || n0 < base) p->fast_ok = 0;
+          prev = n0;
+        }
+      }
+    }
+
     // Row k holds a voxel with no weight at all (so max_j V includes 0)?
     p->hYinit.resize(nrows);
     for (int64_t k = 0; k < nrows; ++k) {

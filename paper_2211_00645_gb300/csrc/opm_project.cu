@@ -2,29 +2,38 @@
 // the deskewed volume, computed straight from the raw stack without ever
 // writing the volume.
 //
-// Work decomposition (one CTA = 32 output columns j x X output columns x):
+// Work decomposition (one CTA = 32 output columns j x 128 output columns x):
 //  * Output row k of the volume reads only camera row k of the raw stack, at
-//    the planes n0(j,k), n0(j,k)+1 of the CTA's 32 columns: a contiguous slab
-//    of P planes.  A producer warp stages that slab, {X cols, 1 row, P planes},
+//    planes n0(j,k), n0(j,k)+1 of the CTA's 32 columns: a contiguous slab of P
+//    planes.  A producer warp stages that slab, {128 x, 1 row, P planes},
 //    into shared memory with one TMA load per row, several rows ahead, on an
 //    mbarrier ring.  Planes outside [0, nscan) arrive as TMA zero fill, which
 //    is exactly the zero padding of the interpolation.
-//  * Four compute warps own 8 columns j each and VEC columns x per lane.  For
+//  * Four compute warps own 8 columns j each and 4 columns x per lane.  For
 //    every staged row they walk their 8 columns in order, keeping the current
-//    plane pair (a, b - a) in registers; a column that moves to the next plane
-//    costs one shared-memory vector load, so each staged raw value is
+//    plane pair (a, b - a) in registers: a column that moves to the next
+//    plane costs one shared-memory load, so each staged raw value is
 //    converted to FP32 once per warp rather than once per voxel.  Plane steps
-//    are warp-uniform bit masks computed by the producer.
-//  * z-reductions (max, sum, first argmax) stay in registers across rows; the
-//    y-max of each row is reduced over the CTA's 32 columns in shared memory
-//    and folded into the global y-MIP with one coalesced atomic max per
-//    column (max is order independent, so the result is deterministic).
+//    come as warp-uniform bit masks from the producer.
+//  * z-reductions stay in registers across rows; the y-max of each row is
+//    reduced over the CTA's 32 columns in shared memory and folded into the
+//    global y-MIP with one coalesced atomic max per column (max is order
+//    independent, so the result is deterministic).
 //  * Only rows whose band can carry non-zero weight for the tile are visited;
 //    all other rows are exactly zero and enter the maxima as the value 0.
-// The fast variant (uint16 input, z-MIP and/or y-MIP only) stages two rows per
-// step so that the z-max takes one 3-input max per voxel pair, uses packed
-// FP32x2 FMAs, and splits each tile's row band into chunks whose z-maxima are
-// combined with atomic max, which balances tiles of very different band length.
+//
+// Two kernels share that structure:
+//  k_project_fast  uint16 input, z-MIP and/or y-MIP, full 32-column tiles of
+//                  plans whose columns never skip a plane (checked on the
+//                  host with the kernel's own arithmetic).  Two rows per stage
+//                  (one 3-input max per voxel pair into the z-max), packed
+//                  FP32x2 FMAs, one branch per column step, and each tile's
+//                  row band split into 128-row chunks whose z-maxima combine
+//                  by atomic max, which balances tiles of very different band
+//                  length.
+//  k_project_gen   every output (z-sum, first argmax), uint16 or FP32 input,
+//                  any tile (partial last tile, column steps of several
+//                  planes), one row per stage, whole band per CTA.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -40,10 +49,13 @@ namespace {
 
 constexpr int kNW = 4;               // compute warps per CTA
 constexpr int kJT = kTileJ / kNW;    // columns j per compute warp (8)
-constexpr int kStages = 4;           // TMA ring depth
 constexpr int kThreads = 32 * (kNW + 1);
-constexpr int kChunkRows = 128;      // rows per work unit in the fast variant
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: the kernel itself takes < 10 ms
+constexpr int kVec = 4;              // columns x per lane
+constexpr int kX = 32 * kVec;        // columns x per CTA
+constexpr int kChunkRows = 128;      // rows per work unit of the fast kernel
+constexpr int kStagesFast = 6;       // TMA ring depth, fast kernel
+constexpr int kStagesGen = 4;        // TMA ring depth, general kernel
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a launch takes < 10 ms
 
 static_assert(kJT * kNW == kTileJ, "tile");
 
@@ -158,8 +170,7 @@ __device__ __forceinline__ f2 u16x2_to_f2(uint32_t w) {
   return sub2(r, pk(8388608.0f, 8388608.0f));
 }
 
-// Float max on 32-bit words, valid for any sign (+0 and -0 compare equal up
-// to their bit patterns; both are exact maxima of the same voxel set).
+// Float max on 32-bit words, valid for any sign.
 __device__ __forceinline__ void atomic_max_f(float* addr, float v) {
   if (v >= 0.0f)
     atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
@@ -167,44 +178,90 @@ __device__ __forceinline__ void atomic_max_f(float* addr, float v) {
     atomicMin(reinterpret_cast<unsigned*>(addr), __float_as_uint(v));
 }
 
-// --------------------------------------------------------------- layout
-struct __align__(16) RowHdr {
-  int k;           // camera row staged (>= nz: padding row, all zero)
-  int nlo;         // first staged plane
-  unsigned adv;    // bit j: column j is one plane above column j-1
-  unsigned jump;   // bit j: column j is more than one plane above column j-1
-  unsigned valid;  // bit j: column j lies inside the output grid
-  int ofirst[kNW]; // slab offset of the first column of each compute warp
-  int pad[3];
-};
-static_assert(sizeof(RowHdr) == 48, "hdr");
-
-template <typename T, int VEC, int ROWS>
-struct Layout {
-  static constexpr int X = 32 * VEC;  // columns x per CTA
-  // slab rows 0..P-1 come from TMA, rows P and P+1 stay zero
-  __host__ __device__ static size_t slab_row_bytes(int P) { return (size_t)(P + 2) * X * sizeof(T); }
-  __host__ __device__ static size_t slab_stage_bytes(int P) { return ROWS * slab_row_bytes(P); }
-  __host__ __device__ static size_t off_w(int P) { return kStages * slab_stage_bytes(P); }
-  __host__ __device__ static size_t off_o(int P) { return off_w(P) + kStages * ROWS * kTileJ * 4; }
-  __host__ __device__ static size_t off_hdr(int P) { return off_o(P) + kStages * ROWS * kTileJ * 4; }
-  __host__ __device__ static size_t off_y(int P) { return off_hdr(P) + kStages * ROWS * sizeof(RowHdr); }
-  __host__ __device__ static size_t off_bar(int P) { return off_y(P) + kStages * ROWS * X * 4; }
-  __host__ __device__ static size_t total(int P) { return off_bar(P) + 2 * kStages * 8; }
-};
-
-// Conflict-free index of column xl (= 8*L + c for VEC = 8) in the y-max
-// buffer: both the compute lanes (fixed c, 32 consecutive L) and the
-// producer lanes (32 consecutive xl) hit 32 distinct banks.
-template <int VEC>
+// Conflict-free index of column xl = 4L + c (L = owning lane) in a y-max
+// buffer: the compute lanes (fixed c, 32 consecutive L) and the producer
+// lanes (32 consecutive xl) both hit 32 distinct banks.
 __device__ __forceinline__ int yidx(int xl) {
-  if constexpr (VEC == 8) {
-    const int L = xl >> 3;
-    return (L << 3) + ((xl & 7) ^ ((L >> 2) & 7));
+  const int L = xl >> 2;
+  return (L << 2) + ((xl & 3) ^ ((L >> 3) & 3));
+}
+
+// 4 raw values of one staged row (this lane's 4 columns) as two FP32 pairs.
+template <typename T>
+__device__ __forceinline__ void lds_row(const unsigned char* p, f2 (&out)[2]) {
+  if constexpr (std::is_same<T, uint16_t>::value) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    out[0] = u16x2_to_f2(u.x);
+    out[1] = u16x2_to_f2(u.y);
   } else {
-    const int L = xl >> 2;
-    return (L << 2) + ((xl & 3) ^ ((L >> 3) & 3));
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    out[0] = pk(f.x, f.y);
+    out[1] = pk(f.z, f.w);
   }
+}
+
+// One staged row's streaming state for a compute lane: the lower plane a
+// and the difference d = b - a at slab offset o.
+struct Stream {
+  f2 a[2];
+  f2 d[2];
+  int o;
+};
+
+template <typename T>
+__device__ __forceinline__ void stream_reset(Stream& st, const unsigned char* lane_slab, int pitch, int o) {
+  f2 b[2];
+  st.o = o;
+  lds_row<T>(lane_slab + o * pitch, st.a);
+  lds_row<T>(lane_slab + (o + 1) * pitch, b);
+  st.d[0] = sub2(b[0], st.a[0]);
+  st.d[1] = sub2(b[1], st.a[1]);
+}
+
+template <typename T>
+__device__ __forceinline__ void stream_step(Stream& st, const unsigned char* lane_slab, int pitch) {
+  f2 b[2];
+  st.o += 1;
+  lds_row<T>(lane_slab + (st.o + 1) * pitch, b);
+  if constexpr (std::is_same<T, uint16_t>::value) {
+    // integers below 2^24: a + (b - a) == b exactly
+    st.a[0] = add2(st.a[0], st.d[0]);
+    st.a[1] = add2(st.a[1], st.d[1]);
+  } else {
+    lds_row<T>(lane_slab + st.o * pitch, st.a);
+  }
+  st.d[0] = sub2(b[0], st.a[0]);
+  st.d[1] = sub2(b[1], st.a[1]);
+}
+
+// Same streaming on 32-bit shared-memory offsets (uint16 slab, fast kernel):
+// keeps addresses in single registers next to the smem base symbol.
+__device__ __forceinline__ void lds_row_u16(const unsigned char* smem, uint32_t off, f2 (&out)[2]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(smem + off);
+  out[0] = u16x2_to_f2(u.x);
+  out[1] = u16x2_to_f2(u.y);
+}
+
+__device__ __forceinline__ void stream_reset_u16(Stream& st, const unsigned char* smem, uint32_t lane_off,
+                                                 uint32_t pitch, int o) {
+  f2 b[2];
+  st.o = o;
+  lds_row_u16(smem, lane_off + o * pitch, st.a);
+  lds_row_u16(smem, lane_off + (o + 1) * pitch, b);
+  st.d[0] = sub2(b[0], st.a[0]);
+  st.d[1] = sub2(b[1], st.a[1]);
+}
+
+__device__ __forceinline__ void stream_step_u16(Stream& st, const unsigned char* smem, uint32_t lane_off,
+                                                uint32_t pitch) {
+  f2 b[2];
+  st.o += 1;
+  lds_row_u16(smem, lane_off + (st.o + 1) * pitch, b);
+  // integers below 2^24: a + (b - a) == b exactly
+  st.a[0] = add2(st.a[0], st.d[0]);
+  st.a[1] = add2(st.a[1], st.d[1]);
+  st.d[0] = sub2(b[0], st.a[0]);
+  st.d[1] = sub2(b[1], st.a[1]);
 }
 
 struct ProjArgs {
@@ -214,124 +271,320 @@ struct ProjArgs {
   float* ymip;
   int32_t* argz;
   int P;       // staged planes per row
-  int kchunk;  // rows per work unit (fast variant)
+  int kchunk;  // rows per work unit (fast kernel)
+  int jt0;     // first j-tile of this launch
 };
-
-// Load VEC raw values of one staged row for this lane and return them as
-// FP32 pairs.
-template <typename T, int VEC>
-__device__ __forceinline__ void lds_row(const unsigned char* p, f2 (&out)[VEC / 2]) {
-  if constexpr (std::is_same<T, uint16_t>::value && VEC == 8) {
-    const uint4 u = *reinterpret_cast<const uint4*>(p);
-    out[0] = u16x2_to_f2(u.x);
-    out[1] = u16x2_to_f2(u.y);
-    out[2] = u16x2_to_f2(u.z);
-    out[3] = u16x2_to_f2(u.w);
-  } else if constexpr (std::is_same<T, uint16_t>::value && VEC == 4) {
-    const uint2 u = *reinterpret_cast<const uint2*>(p);
-    out[0] = u16x2_to_f2(u.x);
-    out[1] = u16x2_to_f2(u.y);
-  } else {
-    static_assert(std::is_same<T, float>::value && VEC == 4, "vector shape");
-    const float4 f = *reinterpret_cast<const float4*>(p);
-    out[0] = pk(f.x, f.y);
-    out[1] = pk(f.z, f.w);
-  }
-}
-
-// One staged row's streaming state for a compute lane.
-template <int VEC>
-struct Stream {
-  f2 a[VEC / 2];  // R~[o]
-  f2 d[VEC / 2];  // R~[o+1] - R~[o]
-  int o;          // slab offset of the current lower plane
-};
-
-template <typename T, int VEC>
-__device__ __forceinline__ void stream_reset(Stream<VEC>& st, const unsigned char* slab, size_t pitch,
-                                             int o) {
-  f2 b[VEC / 2];
-  st.o = o;
-  lds_row<T, VEC>(slab + (size_t)o * pitch, st.a);
-  lds_row<T, VEC>(slab + (size_t)(o + 1) * pitch, b);
-#pragma unroll
-  for (int i = 0; i < VEC / 2; ++i) st.d[i] = sub2(b[i], st.a[i]);
-}
-
-template <typename T, int VEC>
-__device__ __forceinline__ void stream_step(Stream<VEC>& st, const unsigned char* slab, size_t pitch) {
-  f2 b[VEC / 2];
-  st.o += 1;
-  lds_row<T, VEC>(slab + (size_t)(st.o + 1) * pitch, b);
-  if constexpr (std::is_same<T, uint16_t>::value) {
-    // integers below 2^24: a + (b - a) == b exactly
-#pragma unroll
-    for (int i = 0; i < VEC / 2; ++i) {
-      st.a[i] = add2(st.a[i], st.d[i]);
-      st.d[i] = sub2(b[i], st.a[i]);
-    }
-  } else {
-    f2 a[VEC / 2];
-    lds_row<T, VEC>(slab + (size_t)st.o * pitch, a);
-#pragma unroll
-    for (int i = 0; i < VEC / 2; ++i) {
-      st.a[i] = a[i];
-      st.d[i] = sub2(b[i], a[i]);
-    }
-  }
-}
 
 // =====================================================================
-// TMA kernel.  FAST: uint16, two rows per stage, z-MIP/y-MIP only, row band
-// split into chunks (z-MIP combined with atomic max).  !FAST: one row per
-// stage, every output, whole row band per CTA.
-template <typename T, int VEC, int ROWS, bool FAST>
-__global__ void __launch_bounds__(kThreads, 1)
-k_project_tma(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
-  using L = Layout<T, VEC, ROWS>;
-  constexpr int X = L::X;
+// Fast kernel: uint16, z-MIP and/or y-MIP, full tiles, unit column steps.
+namespace fast {
+
+constexpr int S = kStagesFast;
+
+struct __align__(8) WarpRec {
+  unsigned adv;  // bit j (1..7): column j sits one plane above column j-1
+  int ofirst;    // slab offset of the warp's first column
+};
+
+__host__ __device__ inline size_t slab_row_bytes(int P) { return (size_t)P * kX * 2; }
+__host__ __device__ inline size_t stage_slab_bytes(int P) { return 2 * slab_row_bytes(P); }
+__host__ __device__ inline size_t off_w(int P) { return S * stage_slab_bytes(P); }         // float2 [S][2][32]
+__host__ __device__ inline size_t off_rec(int P) { return off_w(P) + S * 2 * kTileJ * 8; }  // WarpRec [S][2][4]
+__host__ __device__ inline size_t off_k(int P) { return off_rec(P) + S * 2 * kNW * 8; }     // int [S][2]
+__host__ __device__ inline size_t off_ybuf(int P) { return off_k(P) + S * 2 * 8; }          // float [S][2][kX]
+__host__ __device__ inline size_t off_bar(int P) { return off_ybuf(P) + S * 2 * kX * 4; }
+__host__ __device__ inline size_t total(int P) { return off_bar(P) + 2 * S * 8; }
+
+}  // namespace fast
+
+__global__ void __launch_bounds__(kThreads, 4)
+k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
+  using namespace fast;
   const PlanView& v = args.v;
   const int P = args.P;
-  const int jt = blockIdx.x;
+  const int jt = blockIdx.x + args.jt0;
   const int j0 = jt * kTileJ;
-  const int xbase = blockIdx.z * X;
+  const int xbase = blockIdx.z * kX;
   const Band band = v.band[jt];
-  int ks = band.lo, ke = band.hi;
-  if constexpr (FAST) {
-    ks = max(ks, (int)blockIdx.y * args.kchunk);
-    ke = min(ke, ((int)blockIdx.y + 1) * args.kchunk);
-    if (ks >= ke) return;
-  }
-  const int nst = (ke - ks + ROWS - 1) / ROWS;
+  const int ks = max(band.lo, (int)blockIdx.y * args.kchunk);
+  const int ke = min(band.hi, ((int)blockIdx.y + 1) * args.kchunk);
+  if (ks >= ke) return;
+  const int nst = (ke - ks + 1) / 2;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  const size_t pitch = (size_t)X * sizeof(T);
-  float* wtab = reinterpret_cast<float*>(smem + L::off_w(P));
-  int* otab = reinterpret_cast<int*>(smem + L::off_o(P));
-  RowHdr* hdr = reinterpret_cast<RowHdr*>(smem + L::off_hdr(P));
-  float* ybuf = reinterpret_cast<float*>(smem + L::off_y(P));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar(P));
-  uint64_t* ydone = full + kStages;
-  auto slab = [&](int s, int r) { return smem + (size_t)s * L::slab_stage_bytes(P) + (size_t)r * L::slab_row_bytes(P); };
-  const float yreset = FAST ? 0.0f : -INFINITY;
+  const uint32_t pitch = kX * 2;
+  float2* wtab = reinterpret_cast<float2*>(smem + off_w(P));
+  WarpRec* rec = reinterpret_cast<WarpRec*>(smem + off_rec(P));
+  int* ktab = reinterpret_cast<int*>(smem + off_k(P));
+  float* ybuf = reinterpret_cast<float*>(smem + off_ybuf(P));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + off_bar(P));
+  uint64_t* ydone = full + S;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&ydone[s], kNW);
     }
     fence_barrier_init();
   }
-  // zero rows P, P+1 of every staged row; reset the y-max buffers
-  for (int s = 0; s < kStages; ++s)
-    for (int r = 0; r < ROWS; ++r) {
-      uint4* z = reinterpret_cast<uint4*>(slab(s, r) + (size_t)P * pitch);
-      for (int i = threadIdx.x; i < (int)(2 * pitch / 16); i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < S * 2 * kX; i += kThreads) ybuf[i] = 0.0f;
+  __syncthreads();
+
+  if (warp == 0) {
+    // ------------------------------------------------------ producer warp
+    const Split a = v.A[j0 + lane];
+    int kbase = ks;  // row terms B[k] for 32 rows per load, one group ahead
+    Split bcur = v.B[min(kbase + lane, v.nz - 1)];
+    Split bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
+    bool ok = true;
+    int issued = 0;
+#pragma unroll 1
+    for (int it = 0; it < nst + S && ok; ++it) {
+      if (it >= S) {
+        // retire stage it - S: fold its y-max into the global y-MIP
+        const int r_it = it - S;
+        const int s = r_it % S;
+        ok = mbar_wait(&ydone[s], (r_it / S) & 1, v.err);
+        if (!ok) break;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int k = ktab[s * 2 + r];
+          float* yb = ybuf + (s * 2 + r) * kX;
+#pragma unroll
+          for (int i = 0; i < kVec; ++i) {
+            const int xl = 32 * i + lane;
+            const int yi = yidx(xl);
+            const float val = yb[yi];
+            yb[yi] = 0.0f;
+            if (args.ymip && k < v.nz && xbase + xl < v.nx)
+              atomicMax(reinterpret_cast<int*>(args.ymip + (size_t)k * v.nx + xbase + xl), __float_as_int(val));
+          }
+        }
+        __syncwarp();
+      }
+      if (it < nst) {
+        const int s = it % S;
+        int nlo[2], kk[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int k = ks + 2 * it + r;
+          kk[r] = k;
+          if (k - kbase >= 32) {  // warp-uniform: rows advance in order
+            kbase += 32;
+            bcur = bnext;
+            bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
+          }
+          Split b;
+          b.i = __shfl_sync(0xffffffffu, bcur.i, k - kbase);
+          b.f = __shfl_sync(0xffffffffu, bcur.f, k - kbase);
+          int n0;
+          float w;
+          plane_weight(a, b, v.linear, n0, w);
+          int lo = __shfl_sync(0xffffffffu, n0, 0);
+          int o = n0 - lo;
+          if (k >= v.nz) {  // padding row: staged as zeros, contributes nothing
+            o = 0;
+            w = 0.0f;
+            lo = 0;
+          } else if (o < 0 || o > P - 2) {
+            atomicOr(v.err, kErrSlabRange);
+            o = min(max(o, 0), P - 2);
+          }
+          nlo[r] = lo;
+          const int op = __shfl_up_sync(0xffffffffu, o, 1);
+          const bool first = (lane % kJT) == 0;
+          if (!first && o != op && o != op + 1) atomicOr(v.err, kErrSlabRange);
+          const unsigned adv = __ballot_sync(0xffffffffu, !first && o == op + 1);
+          const int of = __shfl_sync(0xffffffffu, o, (lane % kNW) * kJT);
+          wtab[(s * 2 + r) * kTileJ + lane] = make_float2(w, w);
+          if (lane < kNW) {
+            WarpRec wr;
+            wr.adv = (adv >> (kJT * lane)) & ((1u << kJT) - 1u);
+            wr.ofirst = of;
+            rec[(s * 2 + r) * kNW + lane] = wr;
+          }
+        }
+        if (lane == 0) {
+          ktab[s * 2 + 0] = kk[0];
+          ktab[s * 2 + 1] = kk[1];
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive_tx(&full[s], (unsigned)(2 * P * pitch));
+          tma_load_3d(smem + s * stage_slab_bytes(P), &tmap, &full[s], xbase, kk[0], nlo[0]);
+          tma_load_3d(smem + s * stage_slab_bytes(P) + slab_row_bytes(P), &tmap, &full[s], xbase, kk[1],
+                      nlo[1]);
+        }
+        issued = it + 1;
+        __syncwarp();
+      }
     }
-  for (int i = threadIdx.x; i < kStages * ROWS * X; i += kThreads) ybuf[i] = yreset;
+    if (!ok) {
+      for (int q = max(0, issued - S); q < issued; ++q)
+        (void)mbar_wait(&full[q % S], (q / S) & 1, v.err, 50000000ull);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------- compute warps
+  const int g = warp - 1;
+  float zmax[kJT][kVec];
+#pragma unroll
+  for (int j = 0; j < kJT; ++j)
+#pragma unroll
+    for (int c = 0; c < kVec; ++c) zmax[j][c] = 0.0f;  // uint16 voxels are >= 0
+
+#pragma unroll 1
+  for (int it = 0; it < nst; ++it) {
+    const int s = it % S;
+    if (!mbar_wait(&full[s], (it / S) & 1, v.err)) break;
+    const uint32_t lane0 = (uint32_t)(s * stage_slab_bytes(P)) + lane * (kVec * 2);
+    const uint32_t lane1 = lane0 + (uint32_t)slab_row_bytes(P);
+    const WarpRec r0 = rec[(s * 2 + 0) * kNW + g];
+    const WarpRec r1 = rec[(s * 2 + 1) * kNW + g];
+    // warp-uniform step masks (bit j: step before column j)
+    const unsigned adv0 = __ballot_sync(0xffffffffu, lane < kJT && ((r0.adv >> lane) & 1u));
+    const unsigned adv1 = __ballot_sync(0xffffffffu, lane < kJT && ((r1.adv >> lane) & 1u));
+    Stream st0, st1;
+    stream_reset_u16(st0, smem, lane0, pitch, r0.ofirst);
+    stream_reset_u16(st1, smem, lane1, pitch, r1.ofirst);
+    const uint32_t w0off = (uint32_t)off_w(P) + ((s * 2 + 0) * kTileJ + g * kJT) * 8;
+    const uint32_t w1off = w0off + kTileJ * 8;
+
+    float ym0[kVec], ym1[kVec], vp0[kVec], vp1[kVec];
+#pragma unroll
+    for (int c = 0; c < kVec; ++c) ym0[c] = ym1[c] = 0.0f;
+
+#pragma unroll
+    for (int j = 0; j < kJT; ++j) {
+      if (j > 0) {
+        if (adv0 & (1u << j)) stream_step_u16(st0, smem, lane0, pitch);
+        if (adv1 & (1u << j)) stream_step_u16(st1, smem, lane1, pitch);
+      }
+      const f2 w0 = *reinterpret_cast<const f2*>(smem + w0off + j * 8);
+      const f2 w1 = *reinterpret_cast<const f2*>(smem + w1off + j * 8);
+      float v0[kVec], v1[kVec];
+      upk(fma2(w0, st0.d[0], st0.a[0]), v0[0], v0[1]);
+      upk(fma2(w0, st0.d[1], st0.a[1]), v0[2], v0[3]);
+      upk(fma2(w1, st1.d[0], st1.a[0]), v1[0], v1[1]);
+      upk(fma2(w1, st1.d[1], st1.a[1]), v1[2], v1[3]);
+#pragma unroll
+      for (int c = 0; c < kVec; ++c) zmax[j][c] = max3(zmax[j][c], v0[c], v1[c]);
+      if (j & 1) {
+#pragma unroll
+        for (int c = 0; c < kVec; ++c) {
+          ym0[c] = max3(ym0[c], vp0[c], v0[c]);
+          ym1[c] = max3(ym1[c], vp1[c], v1[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < kVec; ++c) {
+          vp0[c] = v0[c];
+          vp1[c] = v1[c];
+        }
+      }
+    }
+    // combine the y-max of the CTA's four warps in shared memory
+    float* yb0 = ybuf + (s * 2 + 0) * kX;
+    float* yb1 = ybuf + (s * 2 + 1) * kX;
+#pragma unroll
+    for (int c = 0; c < kVec; ++c) {
+      const int yi = yidx(lane * kVec + c);
+      atomicMax(reinterpret_cast<int*>(yb0 + yi), __float_as_int(ym0[c]));
+      atomicMax(reinterpret_cast<int*>(yb1 + yi), __float_as_int(ym1[c]));
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ydone[s]);
+  }
+
+  // ------------------------------------------------------------ epilogue
+  if (!args.zmip) return;
+  const int x = xbase + lane * kVec;
+#pragma unroll
+  for (int j = 0; j < kJT; ++j) {
+    float* row = args.zmip + (size_t)(j0 + g * kJT + j) * v.nx;
+#pragma unroll
+    for (int c = 0; c < kVec; ++c)
+      if (x + c < v.nx) atomicMax(reinterpret_cast<int*>(row + x + c), __float_as_int(zmax[j][c]));
+  }
+}
+
+// =====================================================================
+// General kernel: every output, uint16 or FP32, any tile, one row per stage.
+namespace gen {
+
+constexpr int S = kStagesGen;
+
+struct __align__(16) RowHdr {
+  int k;           // camera row staged
+  int nlo;         // first staged plane
+  unsigned adv;    // bit j: column j is one plane above column j-1
+  unsigned jump;   // bit j: column j is more than one plane above column j-1
+  unsigned valid;  // bit j: column j lies inside the output grid
+  int ofirst[kNW]; // slab offset of the first column of each compute warp
+  int pad[3];
+};
+static_assert(sizeof(RowHdr) == 48, "hdr");
+
+// slab rows 0..P-1 come from TMA, rows P and P+1 stay zero (columns j >= ny)
+template <typename T>
+__host__ __device__ inline size_t slab_bytes(int P) { return (size_t)(P + 2) * kX * sizeof(T); }
+template <typename T>
+__host__ __device__ inline size_t off_w(int P) { return S * slab_bytes<T>(P); }
+template <typename T>
+__host__ __device__ inline size_t off_o(int P) { return off_w<T>(P) + S * kTileJ * 4; }
+template <typename T>
+__host__ __device__ inline size_t off_hdr(int P) { return off_o<T>(P) + S * kTileJ * 4; }
+template <typename T>
+__host__ __device__ inline size_t off_ybuf(int P) { return off_hdr<T>(P) + S * sizeof(RowHdr); }
+template <typename T>
+__host__ __device__ inline size_t off_bar(int P) { return off_ybuf<T>(P) + S * kX * 4; }
+template <typename T>
+__host__ __device__ inline size_t total(int P) { return off_bar<T>(P) + 2 * S * 8; }
+
+}  // namespace gen
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1)
+k_project_gen(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
+  using namespace gen;
+  const PlanView& v = args.v;
+  const int P = args.P;
+  const int jt = blockIdx.x + args.jt0;
+  const int j0 = jt * kTileJ;
+  const int xbase = blockIdx.z * kX;
+  const Band band = v.band[jt];
+  const int ks = band.lo, ke = band.hi;
+  const int nst = ke - ks;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int pitch = kX * (int)sizeof(T);
+  float* wtab = reinterpret_cast<float*>(smem + off_w<T>(P));
+  int* otab = reinterpret_cast<int*>(smem + off_o<T>(P));
+  RowHdr* hdr = reinterpret_cast<RowHdr*>(smem + off_hdr<T>(P));
+  float* ybuf = reinterpret_cast<float*>(smem + off_ybuf<T>(P));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + off_bar<T>(P));
+  uint64_t* ydone = full + S;
+  auto slab = [&](int s) { return smem + (size_t)s * slab_bytes<T>(P); };
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&ydone[s], kNW);
+    }
+    fence_barrier_init();
+  }
+  for (int s = 0; s < S; ++s) {
+    uint4* z = reinterpret_cast<uint4*>(slab(s) + (size_t)P * pitch);
+    for (int i = threadIdx.x; i < 2 * pitch / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  for (int i = threadIdx.x; i < S * kX; i += kThreads) ybuf[i] = -INFINITY;
   __syncthreads();
 
   if (warp == 0) {
@@ -339,258 +592,169 @@ k_project_tma(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
     const int jl = j0 + lane;
     const bool jvalid = jl < v.ny;
     const Split a = v.A[jvalid ? jl : v.ny - 1];
+    int kbase = ks;
+    Split bcur = v.B[min(kbase + lane, v.nz - 1)];
+    Split bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
     bool ok = true;
-    int nst_issued = 0;
-    for (int it = 0; it < nst + kStages && ok; ++it) {
-      if (it >= kStages) {
-        // retire stage it - S: fold its y-max into the global y-MIP
-        const int r_it = it - kStages;
-        const int s = r_it % kStages;
-        ok = mbar_wait(&ydone[s], (r_it / kStages) & 1, v.err);
+    int issued = 0;
+#pragma unroll 1
+    for (int it = 0; it < nst + S && ok; ++it) {
+      if (it >= S) {
+        const int r_it = it - S;
+        const int s = r_it % S;
+        ok = mbar_wait(&ydone[s], (r_it / S) & 1, v.err);
         if (!ok) break;
+        const int k = hdr[s].k;
+        float* yb = ybuf + s * kX;
 #pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-          const int k = hdr[s * ROWS + r].k;
-          float* yb = ybuf + (s * ROWS + r) * X;
-#pragma unroll
-          for (int i = 0; i < VEC; ++i) {
-            const int xl = 32 * i + lane;
-            const int yi = yidx<VEC>(xl);
-            const float val = yb[yi];
-            yb[yi] = yreset;
-            if (args.ymip && k < v.nz && xbase + xl < v.nx) {
-              if constexpr (FAST)
-                atomicMax(reinterpret_cast<int*>(args.ymip + (size_t)k * v.nx + xbase + xl), __float_as_int(val));
-              else
-                atomic_max_f(args.ymip + (size_t)k * v.nx + xbase + xl, val);
-            }
-          }
+        for (int i = 0; i < kVec; ++i) {
+          const int xl = 32 * i + lane;
+          const int yi = yidx(xl);
+          const float val = yb[yi];
+          yb[yi] = -INFINITY;
+          if (args.ymip && xbase + xl < v.nx) atomic_max_f(args.ymip + (size_t)k * v.nx + xbase + xl, val);
         }
         __syncwarp();
       }
       if (it < nst) {
-        // issue stage it: plane table of its rows, then the TMA loads
-        const int s = it % kStages;
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-          const int k = ks + it * ROWS + r;
-          const bool kvalid = k < v.nz;
-          const Split b = v.B[kvalid ? k : v.nz - 1];
-          int n0;
-          float w;
-          plane_weight(a, b, v.linear, n0, w);
-          const int nlo = __shfl_sync(0xffffffffu, n0, 0);
-          const bool valid = jvalid && kvalid;
-          int o = n0 - nlo;
-          if (!valid) {
-            o = P;  // the two zero rows
-            w = 0.0f;
-          } else if (o < 0 || o > P - 2) {
-            atomicOr(v.err, kErrSlabRange);
-            o = min(max(o, 0), P - 2);
-          }
-          const int op = __shfl_up_sync(0xffffffffu, o, 1);
-          const bool first = (lane % kJT) == 0;
-          const unsigned adv = __ballot_sync(0xffffffffu, !first && o == op + 1);
-          const unsigned jump = __ballot_sync(0xffffffffu, !first && o != op && o != op + 1);
-          const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-          wtab[(s * ROWS + r) * kTileJ + lane] = w;
-          otab[(s * ROWS + r) * kTileJ + lane] = o;
-          const int of = __shfl_sync(0xffffffffu, o, (lane % kNW) * kJT);
-          RowHdr& h = hdr[s * ROWS + r];
-          if (lane < kNW) h.ofirst[lane] = of;
-          if (lane == 0) {
-            h.k = k;
-            h.nlo = kvalid ? nlo : 0;
-            h.adv = adv;
-            h.jump = jump;
-            h.valid = vmask;
-          }
+        const int s = it % S;
+        const int k = ks + it;
+        if (k - kbase >= 32) {
+          kbase += 32;
+          bcur = bnext;
+          bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
+        }
+        Split b;
+        b.i = __shfl_sync(0xffffffffu, bcur.i, k - kbase);
+        b.f = __shfl_sync(0xffffffffu, bcur.f, k - kbase);
+        int n0;
+        float w;
+        plane_weight(a, b, v.linear, n0, w);
+        const int nlo = __shfl_sync(0xffffffffu, n0, 0);
+        int o = n0 - nlo;
+        if (!jvalid) {
+          o = P;  // the two zero rows
+          w = 0.0f;
+        } else if (o < 0 || o > P - 2) {
+          atomicOr(v.err, kErrSlabRange);
+          o = min(max(o, 0), P - 2);
+        }
+        const int op = __shfl_up_sync(0xffffffffu, o, 1);
+        const bool first = (lane % kJT) == 0;
+        const unsigned adv = __ballot_sync(0xffffffffu, !first && o == op + 1);
+        const unsigned jump = __ballot_sync(0xffffffffu, !first && o != op && o != op + 1);
+        const unsigned vmask = __ballot_sync(0xffffffffu, jvalid);
+        wtab[s * kTileJ + lane] = w;
+        otab[s * kTileJ + lane] = o;
+        const int of = __shfl_sync(0xffffffffu, o, (lane % kNW) * kJT);
+        RowHdr& h = hdr[s];
+        if (lane < kNW) h.ofirst[lane] = of;
+        if (lane == 0) {
+          h.k = k;
+          h.nlo = nlo;
+          h.adv = adv;
+          h.jump = jump;
+          h.valid = vmask;
         }
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive_tx(&full[s], (unsigned)(ROWS * P * pitch));
-#pragma unroll
-          for (int r = 0; r < ROWS; ++r) {
-            const RowHdr& h = hdr[s * ROWS + r];
-            tma_load_3d(slab(s, r), &tmap, &full[s], xbase, h.k, h.nlo);
-          }
+          mbar_arrive_tx(&full[s], (unsigned)(P * pitch));
+          tma_load_3d(slab(s), &tmap, &full[s], xbase, k, nlo);
         }
-        nst_issued = it + 1;
+        issued = it + 1;
         __syncwarp();
       }
     }
     if (!ok) {
-      // on failure, let the copies this warp issued land (bounded) before the
-      // CTA's shared memory is released
-      const int issued = min(nst, nst_issued);
-      for (int q = max(0, issued - kStages); q < issued; ++q)
-        (void)mbar_wait(&full[q % kStages], (q / kStages) & 1, v.err, 50000000ull);
+      for (int q = max(0, issued - S); q < issued; ++q)
+        (void)mbar_wait(&full[q % S], (q / S) & 1, v.err, 50000000ull);
     }
     return;
   }
 
   // -------------------------------------------------------- compute warps
   const int g = warp - 1;
-  const int jg = g * kJT;  // first column of this warp inside the tile
+  const int jg = g * kJT;
   const unsigned lanebit = (lane < kJT) ? (1u << (jg + lane)) : 0u;
-
-  float zmax[kJT][VEC];
-  float zsum[FAST ? 1 : kJT][FAST ? 1 : VEC];
-  int az[FAST ? 1 : kJT][FAST ? 1 : VEC];
-  {
-    const float zinit = (FAST || ks > 0) ? 0.0f : -INFINITY;
+  float zmax[kJT][kVec], zsum[kJT][kVec];
+  int az[kJT][kVec];
+  const float zinit = ks > 0 ? 0.0f : -INFINITY;  // rows before the band are zero
 #pragma unroll
-    for (int j = 0; j < kJT; ++j)
+  for (int j = 0; j < kJT; ++j)
 #pragma unroll
-      for (int c = 0; c < VEC; ++c) zmax[j][c] = zinit;
-    if constexpr (!FAST) {
-#pragma unroll
-      for (int j = 0; j < kJT; ++j)
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) {
-          zsum[j][c] = 0.0f;
-          az[j][c] = 0;
-        }
+    for (int c = 0; c < kVec; ++c) {
+      zmax[j][c] = zinit;
+      zsum[j][c] = 0.0f;
+      az[j][c] = 0;
     }
-  }
 
+#pragma unroll 1
   for (int it = 0; it < nst; ++it) {
-    const int s = it % kStages;
-    if (!mbar_wait(&full[s], (it / kStages) & 1, v.err)) break;
-
-    Stream<VEC> st[ROWS];
-    unsigned adv[ROWS], jump[ROWS], valid[ROWS];
-    int krow[ROWS];
-    float wv[ROWS][kJT];
-    const unsigned char* sl[ROWS];
+    const int s = it % S;
+    if (!mbar_wait(&full[s], (it / S) & 1, v.err)) break;
+    const RowHdr& h = hdr[s];
+    const int krow = h.k;
+    const unsigned adv = __ballot_sync(0xffffffffu, (h.adv & lanebit) != 0);
+    const unsigned jump = __ballot_sync(0xffffffffu, (h.jump & lanebit) != 0);
+    const unsigned valid = __ballot_sync(0xffffffffu, (h.valid & lanebit) != 0);
+    const unsigned char* ls = slab(s) + lane * (kVec * (int)sizeof(T));
+    Stream st;
+    stream_reset<T>(st, ls, pitch, h.ofirst[g]);
+    float ym[kVec];
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-      const RowHdr& h = hdr[s * ROWS + r];
-      krow[r] = h.k;
-      // warp-uniform masks (bit j = column jg + j)
-      adv[r] = __ballot_sync(0xffffffffu, (h.adv & lanebit) != 0);
-      jump[r] = __ballot_sync(0xffffffffu, (h.jump & lanebit) != 0);
-      valid[r] = __ballot_sync(0xffffffffu, (h.valid & lanebit) != 0);
-      const float4* wp = reinterpret_cast<const float4*>(wtab + (s * ROWS + r) * kTileJ + jg);
-#pragma unroll
-      for (int q = 0; q < kJT / 4; ++q) {
-        const float4 w4 = wp[q];
-        wv[r][4 * q + 0] = w4.x;
-        wv[r][4 * q + 1] = w4.y;
-        wv[r][4 * q + 2] = w4.z;
-        wv[r][4 * q + 3] = w4.w;
-      }
-      sl[r] = slab(s, r) + (size_t)lane * VEC * sizeof(T);
-      stream_reset<T, VEC>(st[r], sl[r], pitch, h.ofirst[g]);
-    }
-
-    float ym[ROWS][VEC];
-    float vprev[ROWS][VEC];
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-      for (int c = 0; c < VEC; ++c) ym[r][c] = yreset;
-
+    for (int c = 0; c < kVec; ++c) ym[c] = -INFINITY;
 #pragma unroll
     for (int j = 0; j < kJT; ++j) {
-      float val[ROWS][VEC];
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        if (j > 0) {
-          if (adv[r] & (1u << j)) {
-            stream_step<T, VEC>(st[r], sl[r], pitch);
-          } else if (jump[r] & (1u << j)) {
-            stream_reset<T, VEC>(st[r], sl[r], pitch, otab[(s * ROWS + r) * kTileJ + jg + j]);
-          }
-        }
-        const f2 w2 = pk(wv[r][j], wv[r][j]);
-#pragma unroll
-        for (int i = 0; i < VEC / 2; ++i) upk(fma2(w2, st[r].d[i], st[r].a[i]), val[r][2 * i], val[r][2 * i + 1]);
+      if (j > 0) {
+        if (adv & (1u << j))
+          stream_step<T>(st, ls, pitch);
+        else if (jump & (1u << j))
+          stream_reset<T>(st, ls, pitch, otab[s * kTileJ + jg + j]);
       }
-      // z-reductions
-      if constexpr (ROWS == 2) {
+      const float w = wtab[s * kTileJ + jg + j];
+      const f2 w2 = pk(w, w);
+      float val[kVec];
+      upk(fma2(w2, st.d[0], st.a[0]), val[0], val[1]);
+      upk(fma2(w2, st.d[1], st.a[1]), val[2], val[3]);
 #pragma unroll
-        for (int c = 0; c < VEC; ++c) zmax[j][c] = max3(zmax[j][c], val[0][c], val[1][c]);
-      } else if constexpr (FAST) {
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) zmax[j][c] = fmaxf(zmax[j][c], val[0][c]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) {
-          const float vv = val[0][c];
-          if (vv > zmax[j][c]) {
-            zmax[j][c] = vv;
-            az[j][c] = krow[0];
-          }
-          zsum[j][c] += vv;
+      for (int c = 0; c < kVec; ++c) {
+        if (val[c] > zmax[j][c]) {
+          zmax[j][c] = val[c];
+          az[j][c] = krow;
         }
+        zsum[j][c] += val[c];
       }
-      // y-max over this warp's columns (pairs of columns per 3-input max)
+      if (valid & (1u << j)) {
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        if constexpr (FAST) {
-          if (j & 1) {
-#pragma unroll
-            for (int c = 0; c < VEC; ++c) ym[r][c] = max3(ym[r][c], vprev[r][c], val[r][c]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < VEC; ++c) vprev[r][c] = val[r][c];
-          }
-        } else {
-          if (valid[r] & (1u << j)) {
-#pragma unroll
-            for (int c = 0; c < VEC; ++c) ym[r][c] = fmaxf(ym[r][c], val[r][c]);
-          }
-        }
+        for (int c = 0; c < kVec; ++c) ym[c] = fmaxf(ym[c], val[c]);
       }
     }
-    if constexpr (FAST && (kJT & 1)) {
+    float* yb = ybuf + s * kX;
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) ym[r][c] = fmaxf(ym[r][c], vprev[r][c]);
-    }
-    // combine the y-max of the CTA's four warps in shared memory
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-      float* yb = ybuf + (s * ROWS + r) * X;
-#pragma unroll
-      for (int c = 0; c < VEC; ++c) {
-        float* addr = yb + yidx<VEC>(lane * VEC + c);
-        if constexpr (FAST)
-          atomicMax(reinterpret_cast<int*>(addr), __float_as_int(ym[r][c]));
-        else
-          atomic_max_f(addr, ym[r][c]);
-      }
-    }
+    for (int c = 0; c < kVec; ++c) atomic_max_f(yb + yidx(lane * kVec + c), ym[c]);
     __syncwarp();
     if (lane == 0) mbar_arrive(&ydone[s]);
   }
 
   // ------------------------------------------------------------ epilogue
-  const int x = xbase + lane * VEC;
+  const int x = xbase + lane * kVec;
 #pragma unroll
   for (int j = 0; j < kJT; ++j) {
     const int jj = j0 + jg + j;
     if (jj >= v.ny) break;
     const size_t row = (size_t)jj * v.nx;
 #pragma unroll
-    for (int c = 0; c < VEC; ++c) {
+    for (int c = 0; c < kVec; ++c) {
       if (x + c >= v.nx) break;
-      if constexpr (FAST) {
-        if (args.zmip) atomicMax(reinterpret_cast<int*>(args.zmip + row + x + c), __float_as_int(zmax[j][c]));
-      } else {
-        float zm = zmax[j][c];
-        int a = az[j][c];
-        if (ke < v.nz && zm < 0.0f) {  // rows after the band are exactly zero
-          zm = 0.0f;
-          a = ke;
-        }
-        if (args.zmip) args.zmip[row + x + c] = zm;
-        if (args.zsum) args.zsum[row + x + c] = zsum[j][c];
-        if (args.argz) args.argz[row + x + c] = a;
+      float zm = zmax[j][c];
+      int a = az[j][c];
+      if (ke < v.nz && zm < 0.0f) {  // rows after the band are exactly zero
+        zm = 0.0f;
+        a = ke;
       }
+      if (args.zmip) args.zmip[row + x + c] = zm;
+      if (args.zsum) args.zsum[row + x + c] = zsum[j][c];
+      if (args.argz) args.argz[row + x + c] = a;
     }
   }
 }
@@ -649,13 +813,15 @@ __global__ void k_yproj_plain(PlanView v, const T* __restrict__ raw, float* ymip
   ymip[idx] = ym;
 }
 
-// Initial values of the atomically combined outputs.
-__global__ void k_init_outputs(PlanView v, float* zmip, float* ymip, int fast) {
+// Initial values of the atomically combined outputs: the fast kernel folds
+// its z-maxima into zeroed z-MIP rows; the y-MIP starts at 0 for uint16
+// input (every voxel is >= 0) and at the plan's per-row value otherwise.
+__global__ void k_init_outputs(PlanView v, float* zmip, float* ymip, int u16) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nzm = zmip ? (long long)v.ny * v.nx : 0;
   const long long nym = ymip ? (long long)v.nz * v.nx : 0;
   if (idx < nzm) zmip[idx] = 0.0f;
-  if (idx < nym) ymip[idx] = fast ? 0.0f : v.yinit[idx / v.nx];
+  if (idx < nym) ymip[idx] = u16 ? 0.0f : v.yinit[idx / v.nx];
 }
 
 // ------------------------------------------------------------- host side
@@ -689,41 +855,63 @@ int max_optin_smem(int dev) {
   return cache[dev];
 }
 
-template <typename T, int VEC, int ROWS, bool FAST>
-opm_status run_tma(const opm_plan* p, const void* raw, const ProjArgs& args, cudaStream_t s) {
-  using Lt = Layout<T, VEC, ROWS>;
-  const PlanView& v = p->view;
-  const size_t smem = Lt::total(args.P);
-  CUtensorMap map;
-  std::memset(&map, 0, sizeof(map));
+template <typename T>
+opm_status encode_raw(const PlanView& v, const void* raw, int P, CUtensorMap* map) {
+  std::memset(map, 0, sizeof(*map));
   const cuuint64_t dims[3] = {(cuuint64_t)v.ncols, (cuuint64_t)v.nrows, (cuuint64_t)v.nscan};
   const cuuint64_t strides[2] = {(cuuint64_t)v.ncols * sizeof(T), (cuuint64_t)v.nrows * v.ncols * sizeof(T)};
-  const cuuint32_t box[3] = {(cuuint32_t)Lt::X, 1u, (cuuint32_t)args.P};
+  const cuuint32_t box[3] = {(cuuint32_t)kX, 1u, (cuuint32_t)P};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUtensorMapDataType dt =
       std::is_same<T, uint16_t>::value ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  CUresult cr = encode_fn()(&map, dt, 3, const_cast<void*>(raw), dims, strides, box, estr,
+  CUresult cr = encode_fn()(map, dt, 3, const_cast<void*>(raw), dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) return fail(OPM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+  if (cr != CUDA_SUCCESS)
+    return fail(OPM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+  return OPM_OK;
+}
 
-  auto kern = k_project_tma<T, VEC, ROWS, FAST>;
-  static int attr_set[64] = {0};
-  const int dev = p->device;
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+template <typename K>
+opm_status prepare_kernel(K kern, int dev, int* done) {
+  if (dev >= 0 && dev < 64 && !done[dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin_smem(dev));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    attr_set[dev] = 1;
+    done[dev] = 1;
   }
-  const int jtiles = (v.ny + kTileJ - 1) / kTileJ;
-  const int xtiles = (v.nx + Lt::X - 1) / Lt::X;
-  const int chunks = FAST ? (v.nz + args.kchunk - 1) / args.kchunk : 1;
-  if (jtiles > 0x7fffffff || chunks > 65535 || xtiles > 65535)
-    return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
-  dim3 grid(jtiles, chunks, xtiles);
-  kern<<<grid, kThreads, smem, s>>>(map, args);
+  return OPM_OK;
+}
+
+opm_status launch_fast(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, int full_tiles,
+                       cudaStream_t s) {
+  static int done[64] = {0};
+  opm_status st = prepare_kernel(k_project_fast, p->device, done);
+  if (st != OPM_OK) return st;
+  const PlanView& v = p->view;
+  const int xtiles = (v.nx + kX - 1) / kX;
+  const int chunks = (v.nz + args.kchunk - 1) / args.kchunk;
+  if (chunks > 65535 || xtiles > 65535) return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
+  dim3 grid(full_tiles, chunks, xtiles);
+  k_project_fast<<<grid, kThreads, fast::total(args.P), s>>>(map, args);
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_tma");
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_fast");
+}
+
+template <typename T>
+opm_status launch_gen(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, int tiles,
+                      cudaStream_t s) {
+  static int done[64] = {0};
+  opm_status st = prepare_kernel(k_project_gen<T>, p->device, done);
+  if (st != OPM_OK) return st;
+  const PlanView& v = p->view;
+  const int xtiles = (v.nx + kX - 1) / kX;
+  if (xtiles > 65535) return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
+  dim3 grid(tiles, 1, xtiles);
+  k_project_gen<T><<<grid, kThreads, gen::total<T>(args.P), s>>>(map, args);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_gen");
 }
 
 }  // namespace
@@ -731,24 +919,23 @@ opm_status run_tma(const opm_plan* p, const void* raw, const ProjArgs& args, cud
 opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, float* zmip, float* zsum,
                           float* ymip, int32_t* argz, cudaStream_t s) {
   const PlanView& v = p->view;
-  const size_t es = in_t == OPM_U16 ? 2 : 4;
-  const double pd = std::floor((kTileJ - 1) * p->rho) + 4.0;
-  const int P = pd > 256.0 ? 257 : (int)pd;
-  const bool fast = in_t == OPM_U16 && !zsum && !argz;
-  const int smem_need = (int)(fast ? Layout<uint16_t, 8, 2>::total(P)
-                                   : (in_t == OPM_U16 ? Layout<uint16_t, 4, 1>::total(P)
-                                                      : Layout<float, 4, 1>::total(P)));
+  const bool u16 = in_t == OPM_U16;
+  const size_t es = u16 ? 2 : 4;
+  const int P = p->P;
+  const int smax = max_optin_smem(p->device);
   const bool tma_ok = !p->force_generic && encode_fn() != nullptr && ((uintptr_t)raw % 16 == 0) &&
-                      ((size_t)v.ncols * es) % 16 == 0 && P <= 256 &&
-                      smem_need <= max_optin_smem(p->device);
+                      ((size_t)v.ncols * es) % 16 == 0 && P <= 256;
+  const bool gen_ok = tma_ok && (int)(u16 ? gen::total<uint16_t>(P) : gen::total<float>(P)) <= smax;
+  const int full_tiles = v.ny / kTileJ;
+  const bool fast = gen_ok && u16 && !zsum && !argz && p->fast_ok && full_tiles > 0 && (int)fast::total(P) <= smax;
 
-  if (!tma_ok) {
+  if (!gen_ok) {
     const long long nzx = (long long)v.ny * v.nx, nyx = (long long)v.nz * v.nx;
     const int tb = 256;
     if (zmip || zsum || argz) {
       const long long nb = (nzx + tb - 1) / tb;
       if (nb > 0x7fffffffLL) return fail(OPM_ERR_UNSUPPORTED, "grid too large");
-      if (in_t == OPM_U16)
+      if (u16)
         k_zproj_plain<uint16_t><<<(unsigned)nb, tb, 0, s>>>(v, static_cast<const uint16_t*>(raw), zmip, zsum, argz);
       else
         k_zproj_plain<float><<<(unsigned)nb, tb, 0, s>>>(v, static_cast<const float*>(raw), zmip, zsum, argz);
@@ -758,7 +945,7 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
     if (ymip) {
       const long long nb = (nyx + tb - 1) / tb;
       if (nb > 0x7fffffffLL) return fail(OPM_ERR_UNSUPPORTED, "grid too large");
-      if (in_t == OPM_U16)
+      if (u16)
         k_yproj_plain<uint16_t><<<(unsigned)nb, tb, 0, s>>>(v, static_cast<const uint16_t*>(raw), ymip);
       else
         k_yproj_plain<float><<<(unsigned)nb, tb, 0, s>>>(v, static_cast<const float*>(raw), ymip);
@@ -774,7 +961,7 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
     const long long n = std::max(zinit ? (long long)v.ny * v.nx : 0LL, ymip ? (long long)v.nz * v.nx : 0LL);
     const long long nb = (n + 255) / 256;
     if (nb > 0x7fffffffLL) return fail(OPM_ERR_UNSUPPORTED, "grid too large");
-    k_init_outputs<<<(unsigned)nb, 256, 0, s>>>(v, zinit, ymip, fast ? 1 : 0);
+    k_init_outputs<<<(unsigned)nb, 256, 0, s>>>(v, zinit, ymip, u16 ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch k_init_outputs");
   }
@@ -787,9 +974,18 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
   args.argz = argz;
   args.P = P;
   args.kchunk = kChunkRows;
-  if (fast) return run_tma<uint16_t, 8, 2, true>(p, raw, args, s);
-  if (in_t == OPM_U16) return run_tma<uint16_t, 4, 1, false>(p, raw, args, s);
-  return run_tma<float, 4, 1, false>(p, raw, args, s);
+  args.jt0 = 0;
+  CUtensorMap map;
+  opm_status st = u16 ? encode_raw<uint16_t>(v, raw, P, &map) : encode_raw<float>(v, raw, P, &map);
+  if (st != OPM_OK) return st;
+  const int jtiles = (v.ny + kTileJ - 1) / kTileJ;
+  if (fast) {
+    st = launch_fast(p, map, args, full_tiles, s);
+    if (st != OPM_OK || full_tiles == jtiles) return st;
+    args.jt0 = full_tiles;  // the partial last tile
+    return launch_gen<uint16_t>(p, map, args, jtiles - full_tiles, s);
+  }
+  return u16 ? launch_gen<uint16_t>(p, map, args, jtiles, s) : launch_gen<float>(p, map, args, jtiles, s);
 }
 
 }  // namespace opm

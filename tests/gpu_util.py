@@ -34,7 +34,7 @@ def check_argz(argz_gpu, V, zmip_ref, tol_abs):
     picked = np.take_along_axis(V, a[None].astype(np.int64), axis=0)[0]
     assert np.all(picked >= zmip_ref - tol_abs)
     srt = np.sort(V, axis=0)
-    clear = (srt[-1] - srt[-2]) > 2 * tol_abs
+    clear = (srt[-1] - srt[-2]) > 2 * tol_abs if nz > 1 else np.ones(srt.shape[1:], dtype=bool)
     first = np.argmax(V, axis=0)
     assert np.array_equal(a[clear], first[clear])
 

@@ -1,8 +1,10 @@
 // Full-volume deskew (Fig. 2c remap with linear interpolation between scan
-// planes).  Output-write bound: every voxel is written once with 16-byte
-// streaming stores; each thread walks a run of output columns j of one row k
-// and keeps the current pair of raw planes in registers, so a raw vector is
-// fetched once per plane step rather than once per voxel.
+// planes).  Output-write bound: every voxel is written once with streaming
+// stores.  Each thread walks a run of output columns j of one row k and keeps
+// the current pair of raw planes in registers, so a raw vector is fetched once
+// per plane step rather than once per voxel.  A lane owns two half-vectors of
+// columns 32*HALF apart, so that every store instruction of a warp covers one
+// contiguous span of 32*HALF elements.
 #include "opm_common.cuh"
 
 namespace opm {
@@ -13,34 +15,53 @@ constexpr int kThreadsX = 32;  // lanes along x
 constexpr int kThreadsY = 8;   // j-runs per CTA
 constexpr int kRunJ = 8;       // output columns per thread
 
+template <typename T, int N, typename Acc>
+__device__ __forceinline__ void load_half(const T* __restrict__ p, bool vec, int lim, Acc (&out)[N]) {
+  static_assert(sizeof(T) * N == 8, "8-byte half vectors");
+  if (vec) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const T* e = reinterpret_cast<const T*>(&u);
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = static_cast<Acc>(e[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = i < lim ? static_cast<Acc>(__ldg(p + i)) : Acc(0);
+  }
+}
+
 template <typename Tin, typename Tout, typename Acc, int VEC>
 __global__ void __launch_bounds__(kThreadsX* kThreadsY)
 k_deskew(PlanView v, const Tin* __restrict__ raw, Tout* __restrict__ vol, int xtiles,
          int in_vec_ok, int out_vec_ok) {
+  constexpr int H = VEC / 2;  // elements per half-vector
   const int k = blockIdx.x / xtiles;
   const int xt = blockIdx.x - k * xtiles;
-  const int x0 = (xt * kThreadsX + threadIdx.x) * VEC;
-  if (x0 >= v.nx) return;
-  const int lim = v.nx - x0;  // valid columns of this vector (>= 1)
-  const bool in_vec = in_vec_ok && lim >= VEC;
-  const bool out_vec = out_vec_ok && lim >= VEC;
+  const int xh[2] = {xt * kThreadsX * VEC + (int)threadIdx.x * H,
+                     xt * kThreadsX * VEC + kThreadsX * H + (int)threadIdx.x * H};
+  if (xh[0] >= v.nx) return;
+  const int lim[2] = {v.nx - xh[0], v.nx - xh[1]};  // valid columns of each half
   const int jb = (blockIdx.y * kThreadsY + threadIdx.y) * kRunJ;
   if (jb >= v.ny) return;
   const Split b = v.B[k];
   const size_t plane = (size_t)v.nrows * v.ncols;
-  const Tin* rowp = raw + (size_t)k * v.ncols + x0;
+  const Tin* rowp = raw + (size_t)k * v.ncols;
 
-  Acc a[VEC], bb[VEC], d[VEC];
+  Acc a[2][H], bb[2][H], d[2][H];
 #pragma unroll
-  for (int i = 0; i < VEC; ++i) a[i] = bb[i] = d[i] = Acc(0);
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int i = 0; i < H; ++i) a[h][i] = bb[h][i] = d[h][i] = Acc(0);
   int ocur = -0x40000000;  // plane index held in a[] (none yet)
 
-  auto fetch = [&](int n, Acc(&out)[VEC]) {
-    if (n >= 0 && n < v.nscan) {
-      load_vec<Tin, VEC, Acc>(rowp + (size_t)n * plane, in_vec, lim, out);
-    } else {
+  auto fetch = [&](int n, Acc(&out)[2][H]) {
 #pragma unroll
-      for (int i = 0; i < VEC; ++i) out[i] = Acc(0);
+    for (int h = 0; h < 2; ++h) {
+      if (n >= 0 && n < v.nscan && lim[h] > 0) {
+        load_half<Tin, H, Acc>(rowp + (size_t)n * plane + xh[h], in_vec_ok && lim[h] >= H, lim[h], out[h]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < H; ++i) out[h][i] = Acc(0);
+      }
     }
   };
 
@@ -54,54 +75,71 @@ k_deskew(PlanView v, const Tin* __restrict__ raw, Tout* __restrict__ vol, int xt
     if (n0 != ocur) {
       if (n0 == ocur + 1) {
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) a[i] = bb[i];
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int i = 0; i < H; ++i) a[h][i] = bb[h][i];
       } else {
         fetch(n0, a);
       }
       fetch(n0 + 1, bb);
 #pragma unroll
-      for (int i = 0; i < VEC; ++i) d[i] = bb[i] - a[i];
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int i = 0; i < H; ++i) d[h][i] = bb[h][i] - a[h][i];
       ocur = n0;
     }
-    Acc val[VEC];
+    Tout* orow = vol + ((size_t)k * v.ny + j) * v.nx;
 #pragma unroll
-    for (int i = 0; i < VEC; ++i) val[i] = fma(w, d[i], a[i]);
-
-    Tout* op = vol + ((size_t)k * v.ny + j) * v.nx + x0;
-    if constexpr (std::is_same<Tout, uint16_t>::value) {
-      uint16_t u[VEC];
+    for (int h = 0; h < 2; ++h) {
+      if (lim[h] <= 0) continue;
+      Acc val[H];
 #pragma unroll
-      for (int i = 0; i < VEC; ++i) u[i] = to_u16_rn(val[i]);
-      if (out_vec && VEC == 8) {
-        const uint32_t* q = reinterpret_cast<const uint32_t*>(u);
-        st_cs_v4u(op, q[0], q[1], q[2], q[3]);
-      } else {
-        for (int i = 0; i < VEC && i < lim; ++i) op[i] = u[i];
+      for (int i = 0; i < H; ++i) val[i] = fma(w, d[h][i], a[h][i]);
+      Tout* op = orow + xh[h];
+      const bool full = out_vec_ok && lim[h] >= H;
+      if constexpr (std::is_same<Tout, float>::value && H == 4) {
+        if (full) {
+          st_cs_v4(op, val[0], val[1], val[2], val[3]);
+          continue;
+        }
       }
-    } else if constexpr (std::is_same<Tout, float>::value) {
-      if (out_vec) {
-#pragma unroll
-        for (int i = 0; i < VEC; i += 4) st_cs_v4(op + i, val[i], val[i + 1], val[i + 2], val[i + 3]);
-      } else {
-        for (int i = 0; i < VEC && i < lim; ++i) op[i] = val[i];
+      if constexpr (std::is_same<Tout, uint16_t>::value && H == 4) {
+        if (full) {
+          const uint32_t lo = (uint32_t)to_u16_rn(val[0]) | ((uint32_t)to_u16_rn(val[1]) << 16);
+          const uint32_t hi = (uint32_t)to_u16_rn(val[2]) | ((uint32_t)to_u16_rn(val[3]) << 16);
+          asm volatile("st.global.cs.v2.b32 [%0], {%1, %2};" ::"l"(op), "r"(lo), "r"(hi) : "memory");
+          continue;
+        }
       }
-    } else {
-      for (int i = 0; i < VEC && i < lim; ++i) op[i] = val[i];
+      if constexpr (std::is_same<Tout, float>::value && H == 2) {
+        if (full) {
+          asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(op), "f"(val[0]), "f"(val[1]) : "memory");
+          continue;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        if (i >= lim[h]) break;
+        if constexpr (std::is_same<Tout, uint16_t>::value)
+          op[i] = to_u16_rn(val[i]);
+        else
+          op[i] = (Tout)val[i];
+      }
     }
   }
 }
 
 template <typename Tin, typename Tout, typename Acc, int VEC>
 opm_status run(const opm_plan* p, const void* raw, void* vol, cudaStream_t s) {
+  constexpr int H = VEC / 2;
   const PlanView& v = p->view;
   const int xtiles = (v.nx + kThreadsX * VEC - 1) / (kThreadsX * VEC);
   const long long gx = (long long)xtiles * v.nz;
   const int gy = (v.ny + kThreadsY * kRunJ - 1) / (kThreadsY * kRunJ);
   if (gx > 0x7fffffffLL || gy > 65535)
     return fail(OPM_ERR_UNSUPPORTED, "deskew grid exceeds launch limits");
-  const int in_vec_ok = (v.ncols % VEC == 0) && ((uintptr_t)raw % 16 == 0);
-  const int out_vec_ok = (v.nx % VEC == 0) && ((uintptr_t)vol % 16 == 0) &&
-                         (sizeof(Tout) * VEC) % 16 == 0;
+  const int in_vec_ok = (v.ncols % H == 0) && ((uintptr_t)raw % 8 == 0);
+  const int out_vec_ok = (v.nx % H == 0) && ((uintptr_t)vol % (sizeof(Tout) * H) == 0);
   dim3 block(kThreadsX, kThreadsY);
   dim3 grid((unsigned)gx, (unsigned)gy);
   k_deskew<Tin, Tout, Acc, VEC><<<grid, block, 0, s>>>(

@@ -30,6 +30,28 @@ struct Band {
 
 constexpr int kTileJ = 32;  // j-columns per CTA tile of the projection kernels
 
+// First column of j-tile t: tiles are 32 columns wide, the last one is
+// shifted back to end at ny when ny is not a multiple of 32 (ny >= 32), so
+// that every tile is full; columns shared with the previous tile are
+// computed twice, which max-combined outputs absorb.
+__host__ __device__ inline int tile_j0(int t, int ny) {
+  const int j0 = t * kTileJ;
+  return (ny >= kTileJ && j0 + kTileJ > ny) ? ny - kTileJ : j0;
+}
+
+// Precomputed plane table of one (tile, camera row) for the fast projection
+// kernel, fetched by one bulk copy next to the raw slab.  Compute warp g
+// (columns 8g..8g+7) reads w[8g..8g+7] and rec[g].
+struct FastRec {
+  unsigned adv;  // bit j (1..7): column 8g+j sits one plane above column 8g+j-1
+  int ofirst;    // slab offset (plane - nlo) of column 8g
+};
+struct __align__(16) FastRow {
+  float w[kTileJ][2];  // (w, w) pairs: interpolation weight of each column
+  FastRec rec[4];
+};
+static_assert(sizeof(FastRow) == 288, "FastRow is copied as 288 bytes");
+
 // Error bits recorded by kernels in the plan's device error word.
 enum : unsigned {
   kErrSlabRange = 1u,   // a plane offset fell outside the staged slab
@@ -47,6 +69,8 @@ struct PlanView {
   const Band* band;   // [ceil(ny / kTileJ)]
   const float* yinit; // [nz]  0 if row k has a structurally zero voxel, else -inf
   unsigned* err;      // error word
+  const FastRow* frow;  // [ntile][nz] fast-kernel tables (NULL unless fast_ok)
+  const int* fnlo;      // [ntile][nz] first staged plane of each (tile, row)
   int nscan, nrows, ncols, nz, ny, nx, J0;
   int linear;         // 1 LINEAR, 0 NEAREST
   float rinv;         // step / pixel (float), used only to size search windows
@@ -64,6 +88,8 @@ struct opm_plan {
   std::vector<opm::Split> hA, hB;
   std::vector<opm::Band> hBand;
   std::vector<float> hYinit;
+  std::vector<opm::FastRow> hFrow;  // fast-kernel tables (when fast_ok)
+  std::vector<int> hFnlo;
   int device;        // -1: created without a device
   void* dmem;        // one allocation holding every device table
   opm::PlanView view;

@@ -140,7 +140,7 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
     const int64_t ntile = (ny + kTileJ - 1) / kTileJ;
     p->hBand.resize(ntile);
     for (int64_t t = 0; t < ntile; ++t) {
-      const int64_t j0 = t * kTileJ;
+      const int64_t j0 = tile_j0((int)t, (int)ny);
       const int64_t j1 = std::min<int64_t>(j0 + kTileJ, ny) - 1;
       int64_t lo = nrows, hi = 0;
       for (int64_t k = 0; k < nrows; ++k) {
@@ -161,16 +161,47 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
     // check replays the kernels' own IEEE single-precision plane formula.
     const double Pd = std::floor((kTileJ - 1) * p->rho) + 4.0;
     p->P = Pd > 256.0 ? 257 : (int)Pd;
-    p->fast_ok = (p->rho <= 1.0 && p->P <= 256) ? 1 : 0;
-    for (int64_t t = 0; p->fast_ok && (t + 1) * kTileJ <= ny; ++t) {
+    p->fast_ok = (p->rho <= 1.0 && p->P <= 256 && ny >= kTileJ) ? 1 : 0;
+    for (int64_t t = 0; p->fast_ok && t < ntile; ++t) {
+      const int j0 = tile_j0((int)t, (int)ny);
       for (int64_t k = 0; p->fast_ok && k < nrows; ++k) {
-        const int base = host_n0(p->hA[t * kTileJ], p->hB[k]);
+        const int base = host_n0(p->hA[j0], p->hB[k]);
         int prev = base;
         for (int l = 1; l < kTileJ; ++l) {
-          const int n0 = host_n0(p->hA[t * kTileJ + l], p->hB[k]);
+          const int n0 = host_n0(p->hA[j0 + l], p->hB[k]);
           if ((l % 8) != 0 && n0 != prev && n0 != prev + 1) p->fast_ok = 0;
           if (n0 - base > p->P - 2 || n0 < base) p->fast_ok = 0;
           prev = n0;
+        }
+      }
+    }
+    // The fast kernel's per-(tile, row) tables, from the same formula.
+    if (p->fast_ok) {
+      p->hFrow.resize((size_t)ntile * nrows);
+      p->hFnlo.resize((size_t)ntile * nrows);
+      for (int64_t t = 0; t < ntile; ++t) {
+        const int j0 = tile_j0((int)t, (int)ny);
+        for (int64_t k = 0; k < nrows; ++k) {
+          FastRow& fr = p->hFrow[t * nrows + k];
+          int o[kTileJ];
+          const int nlo = host_n0(p->hA[j0], p->hB[k]);
+          for (int l = 0; l < kTileJ; ++l) {
+            const Split a = p->hA[j0 + l], b = p->hB[k];
+            const float d = a.f - b.f;
+            const bool neg = d < 0.0f;
+            const float w = (interp == OPM_INTERP_LINEAR) ? (neg ? d + 1.0f : d) : 0.0f;
+            fr.w[l][0] = w;
+            fr.w[l][1] = w;
+            o[l] = a.i - b.i - (neg ? 1 : 0) - nlo;
+          }
+          for (int g = 0; g < 4; ++g) {
+            unsigned adv = 0;
+            for (int jj = 1; jj < 8; ++jj)
+              if (o[8 * g + jj] == o[8 * g + jj - 1] + 1) adv |= 1u << jj;
+            fr.rec[g].adv = adv;
+            fr.rec[g].ofirst = o[8 * g];
+          }
+          p->hFnlo[t * nrows + k] = nlo;
         }
       }
     }
@@ -208,7 +239,9 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
   const size_t szB = align256(sizeof(Split) * p->hB.size());
   const size_t szT = align256(sizeof(Band) * p->hBand.size());
   const size_t szY = align256(sizeof(float) * p->hYinit.size());
-  const size_t total = szA + szB + szT + szY + 256;
+  const size_t szF = align256(sizeof(FastRow) * p->hFrow.size());
+  const size_t szN = align256(sizeof(int) * p->hFnlo.size());
+  const size_t total = szA + szB + szT + szY + szF + szN + 256;
   e = cudaMalloc(&p->dmem, total);
   if (e != cudaSuccess) {
     delete p;
@@ -219,11 +252,17 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
   Split* dB = reinterpret_cast<Split*>(base + szA);
   Band* dT = reinterpret_cast<Band*>(base + szA + szB);
   float* dY = reinterpret_cast<float*>(base + szA + szB + szT);
-  unsigned* dE = reinterpret_cast<unsigned*>(base + szA + szB + szT + szY);
+  FastRow* dF = reinterpret_cast<FastRow*>(base + szA + szB + szT + szY);
+  int* dN = reinterpret_cast<int*>(base + szA + szB + szT + szY + szF);
+  unsigned* dE = reinterpret_cast<unsigned*>(base + szA + szB + szT + szY + szF + szN);
   if ((e = cudaMemcpy(dA, p->hA.data(), sizeof(Split) * p->hA.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(dB, p->hB.data(), sizeof(Split) * p->hB.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(dT, p->hBand.data(), sizeof(Band) * p->hBand.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(dY, p->hYinit.data(), sizeof(float) * p->hYinit.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!p->hFrow.empty() &&
+       (e = cudaMemcpy(dF, p->hFrow.data(), sizeof(FastRow) * p->hFrow.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!p->hFnlo.empty() &&
+       (e = cudaMemcpy(dN, p->hFnlo.data(), sizeof(int) * p->hFnlo.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (e = cudaMemset(dE, 0, 256)) != cudaSuccess) {
     cudaFree(p->dmem);
     delete p;
@@ -236,6 +275,8 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
   v.band = dT;
   v.yinit = dY;
   v.err = dE;
+  v.frow = p->hFrow.empty() ? nullptr : dF;
+  v.fnlo = p->hFnlo.empty() ? nullptr : dN;
   v.nscan = (int)nscan;
   v.nrows = (int)nrows;
   v.ncols = (int)ncols;

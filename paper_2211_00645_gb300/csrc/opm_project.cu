@@ -52,7 +52,7 @@ constexpr int kJT = kTileJ / kNW;    // columns j per compute warp (8)
 constexpr int kThreads = 32 * (kNW + 1);
 constexpr int kVec = 4;              // columns x per lane
 constexpr int kX = 32 * kVec;        // columns x per CTA
-constexpr int kChunkRows = 128;      // rows per work unit of the fast kernel
+constexpr int kChunkRows = 64;       // rows per work unit of the fast kernel
 constexpr int kStagesFast = 6;       // TMA ring depth, fast kernel
 constexpr int kStagesGen = 4;        // TMA ring depth, general kernel
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a launch takes < 10 ms
@@ -234,29 +234,41 @@ __device__ __forceinline__ void stream_step(Stream& st, const unsigned char* lan
   st.d[1] = sub2(b[1], st.a[1]);
 }
 
-// Same streaming on 32-bit shared-memory offsets (uint16 slab, fast kernel):
-// keeps addresses in single registers next to the smem base symbol.
+// Streaming on 32-bit shared-memory offsets for the fast kernel (uint16
+// slab): besides the pair (a, d) the lane keeps the raw words of the next
+// plane, loaded right after each step, so that a step converts data already
+// in registers instead of waiting for a shared-memory load.
+struct StreamPF {
+  f2 a[2];
+  f2 d[2];
+  uint2 nxt;  // raw words of plane o + 2
+  int o;
+};
+
 __device__ __forceinline__ void lds_row_u16(const unsigned char* smem, uint32_t off, f2 (&out)[2]) {
   const uint2 u = *reinterpret_cast<const uint2*>(smem + off);
   out[0] = u16x2_to_f2(u.x);
   out[1] = u16x2_to_f2(u.y);
 }
 
-__device__ __forceinline__ void stream_reset_u16(Stream& st, const unsigned char* smem, uint32_t lane_off,
-                                                 uint32_t pitch, int o) {
+__device__ __forceinline__ void stream_reset_u16(StreamPF& st, const unsigned char* smem, uint32_t lane_off,
+                                                 uint32_t pitch, int o, int P) {
   f2 b[2];
   st.o = o;
   lds_row_u16(smem, lane_off + o * pitch, st.a);
   lds_row_u16(smem, lane_off + (o + 1) * pitch, b);
+  st.nxt = *reinterpret_cast<const uint2*>(smem + lane_off + min(o + 2, P - 1) * pitch);
   st.d[0] = sub2(b[0], st.a[0]);
   st.d[1] = sub2(b[1], st.a[1]);
 }
 
-__device__ __forceinline__ void stream_step_u16(Stream& st, const unsigned char* smem, uint32_t lane_off,
-                                                uint32_t pitch) {
+__device__ __forceinline__ void stream_step_u16(StreamPF& st, const unsigned char* smem, uint32_t lane_off,
+                                                uint32_t pitch, int P) {
   f2 b[2];
+  b[0] = u16x2_to_f2(st.nxt.x);
+  b[1] = u16x2_to_f2(st.nxt.y);
   st.o += 1;
-  lds_row_u16(smem, lane_off + (st.o + 1) * pitch, b);
+  st.nxt = *reinterpret_cast<const uint2*>(smem + lane_off + min(st.o + 2, P - 1) * pitch);
   // integers below 2^24: a + (b - a) == b exactly
   st.a[0] = add2(st.a[0], st.d[0]);
   st.a[1] = add2(st.a[1], st.d[1]);
@@ -276,49 +288,56 @@ struct ProjArgs {
 };
 
 // =====================================================================
-// Fast kernel: uint16, z-MIP and/or y-MIP, full tiles, unit column steps.
+// Fast kernel: uint16, z-MIP and/or y-MIP, plans whose full 32-column
+// windows never skip a plane.  Per stage (two camera rows) the producer only
+// waits for a free slot and issues four asynchronous copies: the two raw
+// slabs (TMA) and the two precomputed plane tables (bulk copies).  The
+// compute warps fold the y-max of each stage into the global y-MIP
+// themselves, 32 columns per warp, after an mbarrier rendezvous.
 namespace fast {
 
 constexpr int S = kStagesFast;
 
-struct __align__(8) WarpRec {
-  unsigned adv;  // bit j (1..7): column j sits one plane above column j-1
-  int ofirst;    // slab offset of the warp's first column
-};
-
 __host__ __device__ inline size_t slab_row_bytes(int P) { return (size_t)P * kX * 2; }
 __host__ __device__ inline size_t stage_slab_bytes(int P) { return 2 * slab_row_bytes(P); }
-__host__ __device__ inline size_t off_w(int P) { return S * stage_slab_bytes(P); }         // float2 [S][2][32]
-__host__ __device__ inline size_t off_rec(int P) { return off_w(P) + S * 2 * kTileJ * 8; }  // WarpRec [S][2][4]
-__host__ __device__ inline size_t off_k(int P) { return off_rec(P) + S * 2 * kNW * 8; }     // int [S][2]
-__host__ __device__ inline size_t off_ybuf(int P) { return off_k(P) + S * 2 * 8; }          // float [S][2][kX]
+__host__ __device__ inline size_t off_tab(int P) { return S * stage_slab_bytes(P); }        // FastRow [S][2]
+__host__ __device__ inline size_t off_ybuf(int P) { return off_tab(P) + S * 2 * sizeof(FastRow); }  // float [S][2][kX]
 __host__ __device__ inline size_t off_bar(int P) { return off_ybuf(P) + S * 2 * kX * 4; }
-__host__ __device__ inline size_t total(int P) { return off_bar(P) + 2 * S * 8; }
+__host__ __device__ inline size_t total(int P) { return off_bar(P) + 3 * S * 8; }
 
 }  // namespace fast
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads, 4)
 k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
   using namespace fast;
   const PlanView& v = args.v;
   const int P = args.P;
-  const int jt = blockIdx.x + args.jt0;
-  const int j0 = jt * kTileJ;
-  const int xbase = blockIdx.z * kX;
+  // grid (x-tile, j-tile, chunk): the CTAs sharing a camera row's planes run
+  // side by side, so their slab rows combine into whole DRAM pages.
+  const int jt = blockIdx.y;
+  const int j0 = tile_j0(jt, v.ny);
+  const int xbase = blockIdx.x * kX;
   const Band band = v.band[jt];
-  const int ks = max(band.lo, (int)blockIdx.y * args.kchunk);
-  const int ke = min(band.hi, ((int)blockIdx.y + 1) * args.kchunk);
+  const int ks = max(band.lo, (int)blockIdx.z * args.kchunk);
+  const int ke = min(band.hi, ((int)blockIdx.z + 1) * args.kchunk);
   if (ks >= ke) return;
   const int nst = (ke - ks + 1) / 2;
 
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t pitch = kX * 2;
-  float2* wtab = reinterpret_cast<float2*>(smem + off_w(P));
-  WarpRec* rec = reinterpret_cast<WarpRec*>(smem + off_rec(P));
-  int* ktab = reinterpret_cast<int*>(smem + off_k(P));
+  FastRow* tab = reinterpret_cast<FastRow*>(smem + off_tab(P));
   float* ybuf = reinterpret_cast<float*>(smem + off_ybuf(P));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + off_bar(P));
   uint64_t* ydone = full + S;
+  uint64_t* cdone = full + 2 * S;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -327,6 +346,7 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&ydone[s], kNW);
+      mbar_init(&cdone[s], kNW);
     }
     fence_barrier_init();
   }
@@ -335,97 +355,47 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
 
   if (warp == 0) {
     // ------------------------------------------------------ producer warp
-    const Split a = v.A[j0 + lane];
-    int kbase = ks;  // row terms B[k] for 32 rows per load, one group ahead
-    Split bcur = v.B[min(kbase + lane, v.nz - 1)];
-    Split bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
+    const FastRow* rows = v.frow + (size_t)jt * v.nz;
+    const int* nlos = v.fnlo + (size_t)jt * v.nz;
+    int kbase = ks;  // first staged planes of 32 rows per load, one group ahead
+    int ncur = nlos[min(kbase + lane, v.nz - 1)];
+    int nnext = nlos[min(kbase + 32 + lane, v.nz - 1)];
     bool ok = true;
     int issued = 0;
 #pragma unroll 1
-    for (int it = 0; it < nst + S && ok; ++it) {
-      if (it >= S) {
-        // retire stage it - S: fold its y-max into the global y-MIP
-        const int r_it = it - S;
-        const int s = r_it % S;
-        ok = mbar_wait(&ydone[s], (r_it / S) & 1, v.err);
-        if (!ok) break;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int k = ktab[s * 2 + r];
-          float* yb = ybuf + (s * 2 + r) * kX;
-#pragma unroll
-          for (int i = 0; i < kVec; ++i) {
-            const int xl = 32 * i + lane;
-            const int yi = yidx(xl);
-            const float val = yb[yi];
-            yb[yi] = 0.0f;
-            if (args.ymip && k < v.nz && xbase + xl < v.nx)
-              atomicMax(reinterpret_cast<int*>(args.ymip + (size_t)k * v.nx + xbase + xl), __float_as_int(val));
-          }
-        }
-        __syncwarp();
+    for (int it = 0; it < nst; ++it) {
+      const int s = it % S;
+      if (it >= S && !mbar_wait(&ydone[s], ((it - S) / S) & 1, v.err)) {
+        ok = false;
+        break;
       }
-      if (it < nst) {
-        const int s = it % S;
-        int nlo[2], kk[2];
+      int nlo[2];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int k = ks + 2 * it + r;
-          kk[r] = k;
-          if (k - kbase >= 32) {  // warp-uniform: rows advance in order
-            kbase += 32;
-            bcur = bnext;
-            bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
-          }
-          Split b;
-          b.i = __shfl_sync(0xffffffffu, bcur.i, k - kbase);
-          b.f = __shfl_sync(0xffffffffu, bcur.f, k - kbase);
-          int n0;
-          float w;
-          plane_weight(a, b, v.linear, n0, w);
-          int lo = __shfl_sync(0xffffffffu, n0, 0);
-          int o = n0 - lo;
-          if (k >= v.nz) {  // padding row: staged as zeros, contributes nothing
-            o = 0;
-            w = 0.0f;
-            lo = 0;
-          } else if (o < 0 || o > P - 2) {
-            atomicOr(v.err, kErrSlabRange);
-            o = min(max(o, 0), P - 2);
-          }
-          nlo[r] = lo;
-          const int op = __shfl_up_sync(0xffffffffu, o, 1);
-          const bool first = (lane % kJT) == 0;
-          if (!first && o != op && o != op + 1) atomicOr(v.err, kErrSlabRange);
-          const unsigned adv = __ballot_sync(0xffffffffu, !first && o == op + 1);
-          const int of = __shfl_sync(0xffffffffu, o, (lane % kNW) * kJT);
-          wtab[(s * 2 + r) * kTileJ + lane] = make_float2(w, w);
-          if (lane < kNW) {
-            WarpRec wr;
-            wr.adv = (adv >> (kJT * lane)) & ((1u << kJT) - 1u);
-            wr.ofirst = of;
-            rec[(s * 2 + r) * kNW + lane] = wr;
-          }
+      for (int r = 0; r < 2; ++r) {
+        const int k = ks + 2 * it + r;
+        if (k - kbase >= 32) {  // warp-uniform: rows advance in order
+          kbase += 32;
+          ncur = nnext;
+          nnext = nlos[min(kbase + 32 + lane, v.nz - 1)];
         }
-        if (lane == 0) {
-          ktab[s * 2 + 0] = kk[0];
-          ktab[s * 2 + 1] = kk[1];
-        }
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive_tx(&full[s], (unsigned)(2 * P * pitch));
-          tma_load_3d(smem + s * stage_slab_bytes(P), &tmap, &full[s], xbase, kk[0], nlo[0]);
-          tma_load_3d(smem + s * stage_slab_bytes(P) + slab_row_bytes(P), &tmap, &full[s], xbase, kk[1],
-                      nlo[1]);
-        }
-        issued = it + 1;
-        __syncwarp();
+        nlo[r] = __shfl_sync(0xffffffffu, ncur, k - kbase);
       }
+      if (lane == 0) {
+        const int k0 = ks + 2 * it;
+        const int k1 = k0 + 1;  // k1 == nz: a padding row, staged as TMA zero fill
+        mbar_arrive_tx(&full[s], (unsigned)(2 * P * pitch + 2 * sizeof(FastRow)));
+        tma_load_3d(smem + s * stage_slab_bytes(P), &tmap, &full[s], xbase, k0, nlo[0]);
+        tma_load_3d(smem + s * stage_slab_bytes(P) + slab_row_bytes(P), &tmap, &full[s], xbase, k1,
+                    k1 < v.nz ? nlo[1] : 0);
+        bulk_load(&tab[s * 2 + 0], rows + k0, sizeof(FastRow), &full[s]);
+        bulk_load(&tab[s * 2 + 1], rows + min(k1, v.nz - 1), sizeof(FastRow), &full[s]);
+      }
+      issued = it + 1;
+      __syncwarp();
     }
-    if (!ok) {
-      for (int q = max(0, issued - S); q < issued; ++q)
-        (void)mbar_wait(&full[q % S], (q / S) & 1, v.err, 50000000ull);
-    }
+    // drain: the CTA's shared memory must outlive every copy this warp issued
+    for (int q = max(0, issued - S); q < issued; ++q)
+      if (!mbar_wait(&full[q % S], (q / S) & 1, v.err, ok ? kWaitLimitNs : 50000000ull)) break;
     return;
   }
 
@@ -440,19 +410,20 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
 #pragma unroll 1
   for (int it = 0; it < nst; ++it) {
     const int s = it % S;
-    if (!mbar_wait(&full[s], (it / S) & 1, v.err)) break;
+    const unsigned ph = (it / S) & 1;
+    if (!mbar_wait(&full[s], ph, v.err)) break;
     const uint32_t lane0 = (uint32_t)(s * stage_slab_bytes(P)) + lane * (kVec * 2);
     const uint32_t lane1 = lane0 + (uint32_t)slab_row_bytes(P);
-    const WarpRec r0 = rec[(s * 2 + 0) * kNW + g];
-    const WarpRec r1 = rec[(s * 2 + 1) * kNW + g];
+    const FastRec r0 = tab[s * 2 + 0].rec[g];
+    const FastRec r1 = tab[s * 2 + 1].rec[g];
     // warp-uniform step masks (bit j: step before column j)
     const unsigned adv0 = __ballot_sync(0xffffffffu, lane < kJT && ((r0.adv >> lane) & 1u));
     const unsigned adv1 = __ballot_sync(0xffffffffu, lane < kJT && ((r1.adv >> lane) & 1u));
-    Stream st0, st1;
-    stream_reset_u16(st0, smem, lane0, pitch, r0.ofirst);
-    stream_reset_u16(st1, smem, lane1, pitch, r1.ofirst);
-    const uint32_t w0off = (uint32_t)off_w(P) + ((s * 2 + 0) * kTileJ + g * kJT) * 8;
-    const uint32_t w1off = w0off + kTileJ * 8;
+    StreamPF st0, st1;
+    stream_reset_u16(st0, smem, lane0, pitch, r0.ofirst, P);
+    stream_reset_u16(st1, smem, lane1, pitch, r1.ofirst, P);
+    const uint32_t w0off = (uint32_t)(off_tab(P) + (s * 2 + 0) * sizeof(FastRow)) + g * kJT * 8;
+    const uint32_t w1off = w0off + (uint32_t)sizeof(FastRow);
 
     float ym0[kVec], ym1[kVec], vp0[kVec], vp1[kVec];
 #pragma unroll
@@ -461,8 +432,8 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
 #pragma unroll
     for (int j = 0; j < kJT; ++j) {
       if (j > 0) {
-        if (adv0 & (1u << j)) stream_step_u16(st0, smem, lane0, pitch);
-        if (adv1 & (1u << j)) stream_step_u16(st1, smem, lane1, pitch);
+        if (adv0 & (1u << j)) stream_step_u16(st0, smem, lane0, pitch, P);
+        if (adv1 & (1u << j)) stream_step_u16(st1, smem, lane1, pitch, P);
       }
       const f2 w0 = *reinterpret_cast<const f2*>(smem + w0off + j * 8);
       const f2 w1 = *reinterpret_cast<const f2*>(smem + w1off + j * 8);
@@ -487,7 +458,8 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
         }
       }
     }
-    // combine the y-max of the CTA's four warps in shared memory
+    // y-max: combine the four warps in shared memory, then each warp folds
+    // 32 columns of both rows into the global y-MIP
     float* yb0 = ybuf + (s * 2 + 0) * kX;
     float* yb1 = ybuf + (s * 2 + 1) * kX;
 #pragma unroll
@@ -495,6 +467,22 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
       const int yi = yidx(lane * kVec + c);
       atomicMax(reinterpret_cast<int*>(yb0 + yi), __float_as_int(ym0[c]));
       atomicMax(reinterpret_cast<int*>(yb1 + yi), __float_as_int(ym1[c]));
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&cdone[s]);
+    if (!mbar_wait(&cdone[s], ph, v.err)) break;
+    {
+      const int xl = 32 * g + lane;
+      const int yi = yidx(xl);
+      const float y0 = yb0[yi], y1 = yb1[yi];
+      yb0[yi] = 0.0f;
+      yb1[yi] = 0.0f;
+      const int k0 = ks + 2 * it;
+      if (args.ymip && xbase + xl < v.nx) {
+        atomicMax(reinterpret_cast<int*>(args.ymip + (size_t)k0 * v.nx + xbase + xl), __float_as_int(y0));
+        if (k0 + 1 < v.nz)
+          atomicMax(reinterpret_cast<int*>(args.ymip + (size_t)(k0 + 1) * v.nx + xbase + xl), __float_as_int(y1));
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&ydone[s]);
@@ -553,9 +541,9 @@ k_project_gen(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
   using namespace gen;
   const PlanView& v = args.v;
   const int P = args.P;
-  const int jt = blockIdx.x + args.jt0;
+  const int jt = blockIdx.y + args.jt0;  // grid (x-tile, j-tile): see k_project_fast
   const int j0 = jt * kTileJ;
-  const int xbase = blockIdx.z * kX;
+  const int xbase = blockIdx.x * kX;
   const Band band = v.band[jt];
   const int ks = band.lo, ke = band.hi;
   const int nst = ke - ks;
@@ -884,7 +872,7 @@ opm_status prepare_kernel(K kern, int dev, int* done) {
   return OPM_OK;
 }
 
-opm_status launch_fast(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, int full_tiles,
+opm_status launch_fast(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, int tiles,
                        cudaStream_t s) {
   static int done[64] = {0};
   opm_status st = prepare_kernel(k_project_fast, p->device, done);
@@ -892,8 +880,8 @@ opm_status launch_fast(const opm_plan* p, const CUtensorMap& map, const ProjArgs
   const PlanView& v = p->view;
   const int xtiles = (v.nx + kX - 1) / kX;
   const int chunks = (v.nz + args.kchunk - 1) / args.kchunk;
-  if (chunks > 65535 || xtiles > 65535) return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
-  dim3 grid(full_tiles, chunks, xtiles);
+  if (chunks > 65535 || tiles > 65535) return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
+  dim3 grid(xtiles, tiles, chunks);
   k_project_fast<<<grid, kThreads, fast::total(args.P), s>>>(map, args);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_fast");
@@ -907,8 +895,8 @@ opm_status launch_gen(const opm_plan* p, const CUtensorMap& map, const ProjArgs&
   if (st != OPM_OK) return st;
   const PlanView& v = p->view;
   const int xtiles = (v.nx + kX - 1) / kX;
-  if (xtiles > 65535) return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
-  dim3 grid(tiles, 1, xtiles);
+  if (tiles > 65535) return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
+  dim3 grid(xtiles, tiles, 1);
   k_project_gen<T><<<grid, kThreads, gen::total<T>(args.P), s>>>(map, args);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_gen");
@@ -926,8 +914,7 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
   const bool tma_ok = !p->force_generic && encode_fn() != nullptr && ((uintptr_t)raw % 16 == 0) &&
                       ((size_t)v.ncols * es) % 16 == 0 && P <= 256;
   const bool gen_ok = tma_ok && (int)(u16 ? gen::total<uint16_t>(P) : gen::total<float>(P)) <= smax;
-  const int full_tiles = v.ny / kTileJ;
-  const bool fast = gen_ok && u16 && !zsum && !argz && p->fast_ok && full_tiles > 0 && (int)fast::total(P) <= smax;
+  const bool fast = gen_ok && u16 && !zsum && !argz && p->fast_ok && v.frow && (int)fast::total(P) <= smax;
 
   if (!gen_ok) {
     const long long nzx = (long long)v.ny * v.nx, nyx = (long long)v.nz * v.nx;
@@ -979,12 +966,7 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
   opm_status st = u16 ? encode_raw<uint16_t>(v, raw, P, &map) : encode_raw<float>(v, raw, P, &map);
   if (st != OPM_OK) return st;
   const int jtiles = (v.ny + kTileJ - 1) / kTileJ;
-  if (fast) {
-    st = launch_fast(p, map, args, full_tiles, s);
-    if (st != OPM_OK || full_tiles == jtiles) return st;
-    args.jt0 = full_tiles;  // the partial last tile
-    return launch_gen<uint16_t>(p, map, args, jtiles - full_tiles, s);
-  }
+  if (fast) return launch_fast(p, map, args, jtiles, s);
   return u16 ? launch_gen<uint16_t>(p, map, args, jtiles, s) : launch_gen<float>(p, map, args, jtiles, s);
 }
 

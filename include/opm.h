@@ -141,6 +141,72 @@ opm_status opm_mip_backward(const opm_plan* plan, const float* g_zmip,
                             void* cuda_stream);
 
 /*
+ * Batched live view: one persistent launch computes the fused z-MIP / y-MIP
+ * (as opm_project with U16 input) of many stacks, channels and ROIs of uneven
+ * sizes.  Multi-colour acquisitions split every camera frame into channels,
+ * each deskewed on its own (the paper's channel split in the section "Methods
+ * for the fast processing and visualisation of lightsheet data"); here a
+ * channel is an item whose raw pointer and pitches select its ROI of a
+ * shared frame stack.
+ */
+typedef struct opm_batch opm_batch; /* opaque; owns device + pinned work lists */
+
+typedef struct {
+  const opm_plan* plan; /* geometry of the item: nscan x nrows x ncols     */
+  const uint16_t* raw;  /* device pointer to sample (n=0, r=0, x=0)        */
+  int64_t row_pitch;    /* elements between camera rows (0: ncols)         */
+  int64_t plane_pitch;  /* elements between scan planes (0: nrows*row_pitch) */
+  float* zmip;          /* [ny][nx] device output, or NULL                 */
+  float* ymip;          /* [nz][nx] device output, or NULL                 */
+} opm_batch_item;
+
+/*
+ * opm_batch_create - work lists for up to max_items items and max_units
+ * work units (a unit is one 32-column j-tile x 128-column x-tile x row chunk
+ * of one item).  Allocates device memory and pinned host memory once; the
+ * other batch calls allocate nothing.
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_OUT_OF_MEMORY, OPM_ERR_CUDA.
+ */
+opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out);
+
+/*
+ * opm_batch_set - host-side preparation of the work list (TMA descriptors of
+ * every item, unit list sorted by decreasing length).  kchunk = rows per
+ * unit (0: 64).  Waits until the previous opm_batch_upload of this batch has
+ * completed before overwriting its pinned staging.  Every item's plan must
+ * have pixel <= step (consecutive output columns at most one scan plane
+ * apart) and ny >= 32, and live on the batch's device; raw pointers must be
+ * 16-byte aligned and pitches multiples of 8 elements.
+ * Errors: OPM_ERR_INVALID_ARG (NULL, counts, pitches), OPM_ERR_UNSUPPORTED
+ * (plan not eligible, alignment, capacity exceeded), OPM_ERR_CUDA.
+ */
+opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk);
+
+/* opm_batch_upload - asynchronous copy of the prepared work list to the
+ * device on cuda_stream.  Errors: OPM_ERR_INVALID_ARG, OPM_ERR_CUDA. */
+opm_status opm_batch_upload(opm_batch* b, void* cuda_stream);
+
+/*
+ * opm_batch_launch - zeroes the items' outputs and runs the persistent fused
+ * projection over all units on cuda_stream (ctas_per_sm in 1..4, 0: 4).
+ * Uses only the device copy of the work list, so the two launches can be
+ * captured once in a CUDA graph and replayed after later upload calls with
+ * the same item count, unit count and slab depth.
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_CUDA.
+ */
+opm_status opm_batch_launch(opm_batch* b, int ctas_per_sm, void* cuda_stream);
+
+/* Units, items and shared-memory bytes of the prepared batch (any pointer
+ * may be NULL).  Errors: OPM_ERR_INVALID_ARG. */
+opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes);
+
+/* Synchronising diagnostic, as opm_plan_check for the batch's launches. */
+opm_status opm_batch_check(const opm_batch* b);
+
+/* Frees a batch (NULL accepted).  No work using it may still be queued. */
+opm_status opm_batch_destroy(opm_batch* b);
+
+/*
  * opm_plan_check - synchronising diagnostic (not for the hot path): waits for
  * the plan's device, then reports OPM_ERR_INTERNAL if any kernel launched with
  * this plan recorded a failed internal consistency check (and clears the

@@ -31,6 +31,12 @@ _STATUS = {
     OPM_ERR_INTERNAL: "OPM_ERR_INTERNAL",
 }
 
+class opm_batch_item(ctypes.Structure):
+    """Mirror of the C struct opm_batch_item."""
+    _fields_ = [("plan", ctypes.c_void_p), ("raw", ctypes.c_void_p), ("row_pitch", ctypes.c_int64),
+                ("plane_pitch", ctypes.c_int64), ("zmip", ctypes.c_void_p), ("ymip", ctypes.c_void_p)]
+
+
 # Every symbol the header declares, with its ctypes signature.
 _SIGS = {
     "opm_plan_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
@@ -45,6 +51,14 @@ _SIGS = {
                                         ctypes.c_void_p]),
     "opm_mip_backward": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "opm_plan_check": (ctypes.c_int, [ctypes.c_void_p]),
+    "opm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)]),
+    "opm_batch_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "opm_batch_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "opm_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "opm_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "opm_batch_check": (ctypes.c_int, [ctypes.c_void_p]),
+    "opm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_last_error": (ctypes.c_char_p, []),
     "opm_version": (ctypes.c_int, []),
 }
@@ -247,3 +261,71 @@ def mip_backward(plan: Plan, g_zmip, argz, stream=None):
     g = torch.empty(plan.raw_shape, dtype=torch.float32, device=g_zmip.device)
     opm_mip_backward(plan, g_zmip, argz, g, stream)
     return g
+
+
+# ----------------------------------------------------------------- batches
+class Batch:
+    """Owns an ``opm_batch*``: one persistent launch of the fused z-MIP/y-MIP
+    over many uint16 stacks, channels (strided ROIs) and ROIs."""
+
+    def __init__(self, max_items: int, max_units: int = 1 << 20):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.opm_batch_create(int(max_items), int(max_units), ctypes.byref(h)), "opm_batch_create")
+        self._h = h
+        self.max_items = int(max_items)
+        self._keep = []
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set(self, items, kchunk: int = 0):
+        """items: sequence of dicts {plan, raw, zmip?, ymip?, row_pitch?, plane_pitch?};
+        raw is a uint16 CUDA tensor (a view is fine: its data pointer is the
+        ROI origin and the pitches are elements)."""
+        arr = (opm_batch_item * max(1, len(items)))()
+        keep = []
+        for i, it in enumerate(items):
+            raw = it["raw"]
+            if not raw.is_cuda:
+                raise ValueError("raw must be a CUDA tensor")
+            z, y = it.get("zmip"), it.get("ymip")
+            arr[i] = opm_batch_item(it["plan"].handle.value, raw.data_ptr(), int(it.get("row_pitch", 0)),
+                                    int(it.get("plane_pitch", 0)), z.data_ptr() if z is not None else None,
+                                    y.data_ptr() if y is not None else None)
+            keep.append((it["plan"], raw, z, y))
+        _check(load().opm_batch_set(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items), int(kchunk)),
+               "opm_batch_set")
+        self._keep = keep
+
+    def upload(self, stream=None):
+        _check(load().opm_batch_upload(self._h, _stream(stream)), "opm_batch_upload")
+
+    def launch(self, ctas_per_sm: int = 0, stream=None):
+        _check(load().opm_batch_launch(self._h, int(ctas_per_sm), _stream(stream)), "opm_batch_launch")
+
+    def run(self, ctas_per_sm: int = 0, stream=None):
+        self.upload(stream)
+        self.launch(ctas_per_sm, stream)
+
+    def info(self):
+        n = ctypes.c_int()
+        u = ctypes.c_int64()
+        sm = ctypes.c_int()
+        _check(load().opm_batch_info(self._h, ctypes.byref(n), ctypes.byref(u), ctypes.byref(sm)), "opm_batch_info")
+        return {"items": n.value, "units": u.value, "smem_bytes": sm.value}
+
+    def check(self):
+        _check(load().opm_batch_check(self._h), "opm_batch_check")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load().opm_batch_destroy(self._h), "opm_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -123,3 +123,8 @@ __device__ __forceinline__ void plane_weight(Split a, Split b, int linear,
 #endif
 
 }  // namespace opm
+
+namespace opm {
+// Fast-projection eligibility and slab depth of a plan (host side).
+inline bool plan_fast_ok(const opm_plan* p) { return p && p->fast_ok && p->view.frow != nullptr; }
+}  // namespace opm

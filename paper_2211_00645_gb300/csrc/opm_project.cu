@@ -41,240 +41,11 @@
 #include <cstring>
 #include <mutex>
 
-#include "opm_common.cuh"
+#include "opm_tma.cuh"
 
 namespace opm {
 
 namespace {
-
-constexpr int kNW = 4;               // compute warps per CTA
-constexpr int kJT = kTileJ / kNW;    // columns j per compute warp (8)
-constexpr int kThreads = 32 * (kNW + 1);
-constexpr int kVec = 4;              // columns x per lane
-constexpr int kX = 32 * kVec;        // columns x per CTA
-constexpr int kChunkRows = 64;       // rows per work unit of the fast kernel
-constexpr int kStagesFast = 6;       // TMA ring depth, fast kernel
-constexpr int kStagesGen = 4;        // TMA ring depth, general kernel
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a launch takes < 10 ms
-
-static_assert(kJT * kNW == kTileJ, "tile");
-
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-                   smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait: gives up after `limit_ns`, or at once when another warp of
-// any CTA has already recorded a timeout in the plan's error word.  Returns
-// false (and records the timeout) when it gives up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* err,
-                                          uint64_t limit_ns = kWaitLimitNs) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  for (unsigned i = 1;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 0) {
-      if (*reinterpret_cast<volatile unsigned*>(err) & kErrWaitTimeout) return false;
-      if (globaltimer_ns() - t0 > limit_ns) {
-        atomicOr(err, kErrWaitTimeout);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                            int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
-      "%5}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
-// Packed FP32x2 arithmetic (one instruction per pair on sm_100-family parts).
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void upk(f2 v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-  f2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ float max3(float a, float b, float c) {
-  float d;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-  return d;
-}
-
-// Two uint16 counts -> FP32x2, exactly: build 2^23 + u in the float bit
-// pattern with a byte permute, then subtract 2^23 from both halves.
-__device__ __forceinline__ f2 u16x2_to_f2(uint32_t w) {
-  const uint32_t lo = __byte_perm(w, 0x4B000000u, 0x7610);
-  const uint32_t hi = __byte_perm(w, 0x4B000000u, 0x7632);
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
-  return sub2(r, pk(8388608.0f, 8388608.0f));
-}
-
-// Float max on 32-bit words, valid for any sign.
-__device__ __forceinline__ void atomic_max_f(float* addr, float v) {
-  if (v >= 0.0f)
-    atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
-  else
-    atomicMin(reinterpret_cast<unsigned*>(addr), __float_as_uint(v));
-}
-
-// Conflict-free index of column xl = 4L + c (L = owning lane) in a y-max
-// buffer: the compute lanes (fixed c, 32 consecutive L) and the producer
-// lanes (32 consecutive xl) both hit 32 distinct banks.
-__device__ __forceinline__ int yidx(int xl) {
-  const int L = xl >> 2;
-  return (L << 2) + ((xl & 3) ^ ((L >> 3) & 3));
-}
-
-// 4 raw values of one staged row (this lane's 4 columns) as two FP32 pairs.
-template <typename T>
-__device__ __forceinline__ void lds_row(const unsigned char* p, f2 (&out)[2]) {
-  if constexpr (std::is_same<T, uint16_t>::value) {
-    const uint2 u = *reinterpret_cast<const uint2*>(p);
-    out[0] = u16x2_to_f2(u.x);
-    out[1] = u16x2_to_f2(u.y);
-  } else {
-    const float4 f = *reinterpret_cast<const float4*>(p);
-    out[0] = pk(f.x, f.y);
-    out[1] = pk(f.z, f.w);
-  }
-}
-
-// One staged row's streaming state for a compute lane: the lower plane a
-// and the difference d = b - a at slab offset o.
-struct Stream {
-  f2 a[2];
-  f2 d[2];
-  int o;
-};
-
-template <typename T>
-__device__ __forceinline__ void stream_reset(Stream& st, const unsigned char* lane_slab, int pitch, int o) {
-  f2 b[2];
-  st.o = o;
-  lds_row<T>(lane_slab + o * pitch, st.a);
-  lds_row<T>(lane_slab + (o + 1) * pitch, b);
-  st.d[0] = sub2(b[0], st.a[0]);
-  st.d[1] = sub2(b[1], st.a[1]);
-}
-
-template <typename T>
-__device__ __forceinline__ void stream_step(Stream& st, const unsigned char* lane_slab, int pitch) {
-  f2 b[2];
-  st.o += 1;
-  lds_row<T>(lane_slab + (st.o + 1) * pitch, b);
-  if constexpr (std::is_same<T, uint16_t>::value) {
-    // integers below 2^24: a + (b - a) == b exactly
-    st.a[0] = add2(st.a[0], st.d[0]);
-    st.a[1] = add2(st.a[1], st.d[1]);
-  } else {
-    lds_row<T>(lane_slab + st.o * pitch, st.a);
-  }
-  st.d[0] = sub2(b[0], st.a[0]);
-  st.d[1] = sub2(b[1], st.a[1]);
-}
-
-// Streaming on 32-bit shared-memory offsets for the fast kernel (uint16
-// slab): besides the pair (a, d) the lane keeps the raw words of the next
-// plane, loaded right after each step, so that a step converts data already
-// in registers instead of waiting for a shared-memory load.
-struct StreamPF {
-  f2 a[2];
-  f2 d[2];
-  uint2 nxt;  // raw words of plane o + 2
-  int o;
-};
-
-__device__ __forceinline__ void lds_row_u16(const unsigned char* smem, uint32_t off, f2 (&out)[2]) {
-  const uint2 u = *reinterpret_cast<const uint2*>(smem + off);
-  out[0] = u16x2_to_f2(u.x);
-  out[1] = u16x2_to_f2(u.y);
-}
-
-__device__ __forceinline__ void stream_reset_u16(StreamPF& st, const unsigned char* smem, uint32_t lane_off,
-                                                 uint32_t pitch, int o, int P) {
-  f2 b[2];
-  st.o = o;
-  lds_row_u16(smem, lane_off + o * pitch, st.a);
-  lds_row_u16(smem, lane_off + (o + 1) * pitch, b);
-  st.nxt = *reinterpret_cast<const uint2*>(smem + lane_off + min(o + 2, P - 1) * pitch);
-  st.d[0] = sub2(b[0], st.a[0]);
-  st.d[1] = sub2(b[1], st.a[1]);
-}
-
-__device__ __forceinline__ void stream_step_u16(StreamPF& st, const unsigned char* smem, uint32_t lane_off,
-                                                uint32_t pitch, int P) {
-  f2 b[2];
-  b[0] = u16x2_to_f2(st.nxt.x);
-  b[1] = u16x2_to_f2(st.nxt.y);
-  st.o += 1;
-  st.nxt = *reinterpret_cast<const uint2*>(smem + lane_off + min(st.o + 2, P - 1) * pitch);
-  // integers below 2^24: a + (b - a) == b exactly
-  st.a[0] = add2(st.a[0], st.d[0]);
-  st.a[1] = add2(st.a[1], st.d[1]);
-  st.d[0] = sub2(b[0], st.a[0]);
-  st.d[1] = sub2(b[1], st.a[1]);
-}
 
 struct ProjArgs {
   PlanView v;
@@ -287,216 +58,40 @@ struct ProjArgs {
   int jt0;     // first j-tile of this launch
 };
 
-// =====================================================================
-// Fast kernel: uint16, z-MIP and/or y-MIP, plans whose full 32-column
-// windows never skip a plane.  Per stage (two camera rows) the producer only
-// waits for a free slot and issues four asynchronous copies: the two raw
-// slabs (TMA) and the two precomputed plane tables (bulk copies).  The
-// compute warps fold the y-max of each stage into the global y-MIP
-// themselves, 32 columns per warp, after an mbarrier rendezvous.
-namespace fast {
-
-constexpr int S = kStagesFast;
-
-__host__ __device__ inline size_t slab_row_bytes(int P) { return (size_t)P * kX * 2; }
-__host__ __device__ inline size_t stage_slab_bytes(int P) { return 2 * slab_row_bytes(P); }
-__host__ __device__ inline size_t off_tab(int P) { return S * stage_slab_bytes(P); }        // FastRow [S][2]
-__host__ __device__ inline size_t off_ybuf(int P) { return off_tab(P) + S * 2 * sizeof(FastRow); }  // float [S][2][kX]
-__host__ __device__ inline size_t off_bar(int P) { return off_ybuf(P) + S * 2 * kX * 4; }
-__host__ __device__ inline size_t total(int P) { return off_bar(P) + 3 * S * 8; }
-
-}  // namespace fast
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
+// Fast kernel: one job per CTA.  Grid (x-tile, j-tile, chunk): the CTAs
+// sharing a camera row's planes run side by side, so their slab rows combine
+// into whole DRAM pages.
 __global__ void __launch_bounds__(kThreads, 4)
 k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
-  using namespace fast;
   const PlanView& v = args.v;
-  const int P = args.P;
-  // grid (x-tile, j-tile, chunk): the CTAs sharing a camera row's planes run
-  // side by side, so their slab rows combine into whole DRAM pages.
   const int jt = blockIdx.y;
-  const int j0 = tile_j0(jt, v.ny);
-  const int xbase = blockIdx.x * kX;
   const Band band = v.band[jt];
-  const int ks = max(band.lo, (int)blockIdx.z * args.kchunk);
-  const int ke = min(band.hi, ((int)blockIdx.z + 1) * args.kchunk);
-  if (ks >= ke) return;
-  const int nst = (ke - ks + 1) / 2;
+  FastJob jb;
+  jb.ks = max(band.lo, (int)blockIdx.z * args.kchunk);
+  jb.ke = min(band.hi, ((int)blockIdx.z + 1) * args.kchunk);
+  if (jb.ks >= jb.ke) return;
+  jb.tmap = &tmap;
+  jb.rows = v.frow + (size_t)jt * v.nz;
+  jb.nlos = v.fnlo + (size_t)jt * v.nz;
+  jb.zmip = args.zmip;
+  jb.ymip = args.ymip;
+  jb.nz = v.nz;
+  jb.nx = v.nx;
+  jb.j0 = tile_j0(jt, v.ny);
+  jb.xbase = blockIdx.x * kX;
+  jb.P = args.P;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  const uint32_t pitch = kX * 2;
-  FastRow* tab = reinterpret_cast<FastRow*>(smem + off_tab(P));
-  float* ybuf = reinterpret_cast<float*>(smem + off_ybuf(P));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + off_bar(P));
-  uint64_t* ydone = full + S;
-  uint64_t* cdone = full + 2 * S;
-
+  const FastRing ring = fast_ring(smem, args.P);
+  fast_ring_init(ring);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&ydone[s], kNW);
-      mbar_init(&cdone[s], kNW);
-    }
-    fence_barrier_init();
-  }
-  for (int i = threadIdx.x; i < S * 2 * kX; i += kThreads) ybuf[i] = 0.0f;
-  __syncthreads();
-
+  int g = 0;
   if (warp == 0) {
-    // ------------------------------------------------------ producer warp
-    const FastRow* rows = v.frow + (size_t)jt * v.nz;
-    const int* nlos = v.fnlo + (size_t)jt * v.nz;
-    int kbase = ks;  // first staged planes of 32 rows per load, one group ahead
-    int ncur = nlos[min(kbase + lane, v.nz - 1)];
-    int nnext = nlos[min(kbase + 32 + lane, v.nz - 1)];
-    bool ok = true;
-    int issued = 0;
-#pragma unroll 1
-    for (int it = 0; it < nst; ++it) {
-      const int s = it % S;
-      if (it >= S && !mbar_wait(&ydone[s], ((it - S) / S) & 1, v.err)) {
-        ok = false;
-        break;
-      }
-      int nlo[2];
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int k = ks + 2 * it + r;
-        if (k - kbase >= 32) {  // warp-uniform: rows advance in order
-          kbase += 32;
-          ncur = nnext;
-          nnext = nlos[min(kbase + 32 + lane, v.nz - 1)];
-        }
-        nlo[r] = __shfl_sync(0xffffffffu, ncur, k - kbase);
-      }
-      if (lane == 0) {
-        const int k0 = ks + 2 * it;
-        const int k1 = k0 + 1;  // k1 == nz: a padding row, staged as TMA zero fill
-        mbar_arrive_tx(&full[s], (unsigned)(2 * P * pitch + 2 * sizeof(FastRow)));
-        tma_load_3d(smem + s * stage_slab_bytes(P), &tmap, &full[s], xbase, k0, nlo[0]);
-        tma_load_3d(smem + s * stage_slab_bytes(P) + slab_row_bytes(P), &tmap, &full[s], xbase, k1,
-                    k1 < v.nz ? nlo[1] : 0);
-        bulk_load(&tab[s * 2 + 0], rows + k0, sizeof(FastRow), &full[s]);
-        bulk_load(&tab[s * 2 + 1], rows + min(k1, v.nz - 1), sizeof(FastRow), &full[s]);
-      }
-      issued = it + 1;
-      __syncwarp();
-    }
-    // drain: the CTA's shared memory must outlive every copy this warp issued
-    for (int q = max(0, issued - S); q < issued; ++q)
-      if (!mbar_wait(&full[q % S], (q / S) & 1, v.err, ok ? kWaitLimitNs : 50000000ull)) break;
-    return;
-  }
-
-  // -------------------------------------------------------- compute warps
-  const int g = warp - 1;
-  float zmax[kJT][kVec];
-#pragma unroll
-  for (int j = 0; j < kJT; ++j)
-#pragma unroll
-    for (int c = 0; c < kVec; ++c) zmax[j][c] = 0.0f;  // uint16 voxels are >= 0
-
-#pragma unroll 1
-  for (int it = 0; it < nst; ++it) {
-    const int s = it % S;
-    const unsigned ph = (it / S) & 1;
-    if (!mbar_wait(&full[s], ph, v.err)) break;
-    const uint32_t lane0 = (uint32_t)(s * stage_slab_bytes(P)) + lane * (kVec * 2);
-    const uint32_t lane1 = lane0 + (uint32_t)slab_row_bytes(P);
-    const FastRec r0 = tab[s * 2 + 0].rec[g];
-    const FastRec r1 = tab[s * 2 + 1].rec[g];
-    // warp-uniform step masks (bit j: step before column j)
-    const unsigned adv0 = __ballot_sync(0xffffffffu, lane < kJT && ((r0.adv >> lane) & 1u));
-    const unsigned adv1 = __ballot_sync(0xffffffffu, lane < kJT && ((r1.adv >> lane) & 1u));
-    StreamPF st0, st1;
-    stream_reset_u16(st0, smem, lane0, pitch, r0.ofirst, P);
-    stream_reset_u16(st1, smem, lane1, pitch, r1.ofirst, P);
-    const uint32_t w0off = (uint32_t)(off_tab(P) + (s * 2 + 0) * sizeof(FastRow)) + g * kJT * 8;
-    const uint32_t w1off = w0off + (uint32_t)sizeof(FastRow);
-
-    float ym0[kVec], ym1[kVec], vp0[kVec], vp1[kVec];
-#pragma unroll
-    for (int c = 0; c < kVec; ++c) ym0[c] = ym1[c] = 0.0f;
-
-#pragma unroll
-    for (int j = 0; j < kJT; ++j) {
-      if (j > 0) {
-        if (adv0 & (1u << j)) stream_step_u16(st0, smem, lane0, pitch, P);
-        if (adv1 & (1u << j)) stream_step_u16(st1, smem, lane1, pitch, P);
-      }
-      const f2 w0 = *reinterpret_cast<const f2*>(smem + w0off + j * 8);
-      const f2 w1 = *reinterpret_cast<const f2*>(smem + w1off + j * 8);
-      float v0[kVec], v1[kVec];
-      upk(fma2(w0, st0.d[0], st0.a[0]), v0[0], v0[1]);
-      upk(fma2(w0, st0.d[1], st0.a[1]), v0[2], v0[3]);
-      upk(fma2(w1, st1.d[0], st1.a[0]), v1[0], v1[1]);
-      upk(fma2(w1, st1.d[1], st1.a[1]), v1[2], v1[3]);
-#pragma unroll
-      for (int c = 0; c < kVec; ++c) zmax[j][c] = max3(zmax[j][c], v0[c], v1[c]);
-      if (j & 1) {
-#pragma unroll
-        for (int c = 0; c < kVec; ++c) {
-          ym0[c] = max3(ym0[c], vp0[c], v0[c]);
-          ym1[c] = max3(ym1[c], vp1[c], v1[c]);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < kVec; ++c) {
-          vp0[c] = v0[c];
-          vp1[c] = v1[c];
-        }
-      }
-    }
-    // y-max: combine the four warps in shared memory, then each warp folds
-    // 32 columns of both rows into the global y-MIP
-    float* yb0 = ybuf + (s * 2 + 0) * kX;
-    float* yb1 = ybuf + (s * 2 + 1) * kX;
-#pragma unroll
-    for (int c = 0; c < kVec; ++c) {
-      const int yi = yidx(lane * kVec + c);
-      atomicMax(reinterpret_cast<int*>(yb0 + yi), __float_as_int(ym0[c]));
-      atomicMax(reinterpret_cast<int*>(yb1 + yi), __float_as_int(ym1[c]));
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&cdone[s]);
-    if (!mbar_wait(&cdone[s], ph, v.err)) break;
-    {
-      const int xl = 32 * g + lane;
-      const int yi = yidx(xl);
-      const float y0 = yb0[yi], y1 = yb1[yi];
-      yb0[yi] = 0.0f;
-      yb1[yi] = 0.0f;
-      const int k0 = ks + 2 * it;
-      if (args.ymip && xbase + xl < v.nx) {
-        atomicMax(reinterpret_cast<int*>(args.ymip + (size_t)k0 * v.nx + xbase + xl), __float_as_int(y0));
-        if (k0 + 1 < v.nz)
-          atomicMax(reinterpret_cast<int*>(args.ymip + (size_t)(k0 + 1) * v.nx + xbase + xl), __float_as_int(y1));
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&ydone[s]);
-  }
-
-  // ------------------------------------------------------------ epilogue
-  if (!args.zmip) return;
-  const int x = xbase + lane * kVec;
-#pragma unroll
-  for (int j = 0; j < kJT; ++j) {
-    float* row = args.zmip + (size_t)(j0 + g * kJT + j) * v.nx;
-#pragma unroll
-    for (int c = 0; c < kVec; ++c)
-      if (x + c < v.nx) atomicMax(reinterpret_cast<int*>(row + x + c), __float_as_int(zmax[j][c]));
+    const bool ok = fast_produce(jb, ring, g, v.err, lane);
+    fast_drain(ring, g, ok, v.err);
+  } else {
+    fast_consume(jb, ring, g, v.err, warp - 1, lane);
   }
 }
 

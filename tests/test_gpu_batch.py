@@ -1,0 +1,135 @@
+"""Batched live view: one persistent launch over stacks, channels (strided
+ROIs of a shared frame stack) and ROIs of uneven sizes.  Every item's result
+must equal its stand-alone opm_project result (same arithmetic, max-combined)
+and the oracle; CUDA-graph replay must equal eager launches."""
+import numpy as np
+import pytest
+
+import opm_synth
+import oracle as O
+from gpu_util import assert_close, to_dev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _stack(shape, seed):
+    n, r, c = shape[:3]
+    cfg = opm_synth.StackConfig("b", n, r, c, *shape[3:], n_blobs=10, sigma=(1.0, 3.0), amp=(200.0, 4000.0),
+                                seed=seed)
+    return opm_synth.raw_stack(cfg)
+
+
+def _mixed(lib, seed=0):
+    """Items: two stacks of different shapes and a 2-channel frame stack."""
+    items, refs = [], []
+    for i, shape in enumerate([(64, 128, 128, 30.0, 0.4, 0.115), (33, 50, 264, 45.0, 0.2, 0.115)]):
+        R = _stack(shape, 10 + i + seed)
+        plan = lib.Plan(*shape)
+        raw = to_dev(R, torch)
+        items.append({"plan": plan, "raw": raw,
+                      "zmip": torch.full((plan.ny, plan.nx), -1.0, device="cuda"),
+                      "ymip": torch.full((plan.nz, plan.nx), -1.0, device="cuda")})
+        refs.append((shape, R))
+    # two colour channels side by side in one camera frame: [n][r][2 * 136]
+    ch = (40, 70, 136, 35.0, 0.3, 0.1)
+    R2 = _stack((40, 70, 272, 35.0, 0.3, 0.1), 20 + seed)
+    raw2 = to_dev(R2, torch)
+    plan = lib.Plan(*ch)
+    for c in range(2):
+        items.append({"plan": plan, "raw": raw2[:, :, 136 * c:], "row_pitch": 272, "plane_pitch": 70 * 272,
+                      "zmip": torch.full((plan.ny, plan.nx), -1.0, device="cuda") if c == 0 else None,
+                      "ymip": torch.full((plan.nz, plan.nx), -1.0, device="cuda")})
+        refs.append((ch, np.ascontiguousarray(R2[:, :, 136 * c:136 * (c + 1)])))
+    return items, refs
+
+
+def test_batch_matches_single_and_oracle(lib):
+    items, refs = _mixed(lib)
+    b = lib.Batch(max_items=8)
+    b.set(items)
+    info = b.info()
+    assert info["items"] == 4 and info["units"] > 0
+    b.run()
+    torch.cuda.synchronize()
+    b.check()
+    for it, (shape, R) in zip(items, refs):
+        plan = it["plan"]
+        single = lib.project(plan, to_dev(R, torch), zmip=True, ymip=True)
+        zref, _, yref, _ = O.project(R.astype(np.float64), O.geometry(*shape))
+        if it["zmip"] is not None:
+            assert torch.equal(it["zmip"], single["zmip"])
+            assert_close(it["zmip"].cpu().numpy(), zref, what="batch zmip")
+        assert torch.equal(it["ymip"], single["ymip"])
+        assert_close(it["ymip"].cpu().numpy(), yref, what="batch ymip")
+
+
+@pytest.mark.parametrize("kchunk,ctas", [(16, 1), (64, 2), (256, 4), (1000, 3)])
+def test_batch_tunables_do_not_change_results(lib, kchunk, ctas):
+    items, _ = _mixed(lib)
+    b = lib.Batch(max_items=8)
+    b.set(items, kchunk=0)
+    b.run()
+    ref = [(it["zmip"].clone() if it["zmip"] is not None else None, it["ymip"].clone()) for it in items]
+    b.set(items, kchunk=kchunk)
+    b.run(ctas_per_sm=ctas)
+    torch.cuda.synchronize()
+    for it, (z, y) in zip(items, ref):
+        if z is not None:
+            assert torch.equal(it["zmip"], z)
+        assert torch.equal(it["ymip"], y)
+
+
+def test_batch_graph_replay_equals_eager(lib):
+    items, _ = _mixed(lib)
+    b = lib.Batch(max_items=8)
+    b.set(items)
+    b.upload()
+    b.launch()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        b.launch(stream=s)  # warm-up on the capture stream
+        s.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            b.launch(stream=s)
+    torch.cuda.synchronize()
+    # new data with the same shapes in the same raw buffers (item 2's raw is
+    # the whole two-channel frame stack), then replay
+    items2, refs2 = _mixed(lib, seed=5)
+    for i in range(3):
+        items[i]["raw"].copy_(items2[i]["raw"])
+    graph.replay()
+    torch.cuda.synchronize()
+    replayed = [(it["zmip"].clone() if it["zmip"] is not None else None, it["ymip"].clone()) for it in items]
+    b.launch()
+    torch.cuda.synchronize()
+    for it, (z, y) in zip(items, replayed):
+        if z is not None:
+            assert torch.equal(it["zmip"], z)
+        assert torch.equal(it["ymip"], y)
+    single = lib.project(items[0]["plan"], items2[0]["raw"], zmip=True)
+    assert torch.equal(replayed[0][0], single["zmip"])
+
+
+def test_batch_rejects_bad_items(lib):
+    b = lib.Batch(max_items=2, max_units=8)
+    coarse = lib.Plan(16, 20, 64, 35.0, 0.05, 0.1)            # pixel > step
+    raw = torch.zeros(coarse.raw_shape, dtype=torch.uint16, device="cuda")
+    with pytest.raises(lib.OpmError) as e:
+        b.set([{"plan": coarse, "raw": raw, "zmip": torch.empty((coarse.ny, coarse.nx), device="cuda")}])
+    assert e.value.status == lib.OPM_ERR_UNSUPPORTED
+    plan = lib.Plan(64, 128, 128, 30.0, 0.4, 0.115)
+    raw = torch.zeros(plan.raw_shape, dtype=torch.uint16, device="cuda")
+    z = torch.empty((plan.ny, plan.nx), device="cuda")
+    with pytest.raises(lib.OpmError) as e:
+        b.set([{"plan": plan, "raw": raw, "zmip": z}])        # more units than max_units
+    assert e.value.status == lib.OPM_ERR_UNSUPPORTED
+    with pytest.raises(lib.OpmError) as e:
+        b.set([{"plan": plan, "raw": raw, "zmip": z, "row_pitch": 100}])   # pitch < ncols
+    assert e.value.status == lib.OPM_ERR_INVALID_ARG
+    with pytest.raises(lib.OpmError) as e:
+        b.set([{"plan": plan, "raw": raw, "zmip": z}] * 3)    # more items than max_items
+    assert e.value.status == lib.OPM_ERR_INVALID_ARG

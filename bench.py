@@ -171,6 +171,50 @@ def cpu_baseline(R, cfg, cols, budget_s=20.0):
             "sample": f"first {cols} of {cfg.ncols} x-columns (project + deskew, {t:.1f} s)"}
 
 
+def serve_bench(args, torch):
+    """Serving comparison on the batched-serving workload: the live-view
+    server against the plain per-stack path, first at Poisson arrivals of
+    ``serve_rate`` stacks/s, then with every stack arriving at once."""
+    from paper_2211_00645_gb300.serve import Camera, LiveViewServer, PinnedRing, PlainServer, PlanCache, \
+        serve_stats
+    shapes = opm_synth.serve_shapes(256, seed=11)
+    plans = PlanCache(35.0, 0.3, 0.1)
+    for (n, r, c, _) in set(shapes):
+        plans.get(n, r, c)
+    ring = PinnedRing(args.serve_ring_gb << 30, seed=11)
+    budget = args.serve_budget_gb << 30
+    out = {"workload": "serving: ROIs rows {256,512,1024} x cols {512,1024,2048}, planes 50..400, 2 channels, "
+                       "theta 35, step 0.3, pixel 0.1; z-MIP + y-MIP per channel",
+           "budget_bytes": budget, "ring_bytes": ring.nbytes}
+    phases = [("paced", args.serve_rate, args.serve_paced), ("saturated", None, args.serve_saturated)]
+
+    def one(make, rate, n, seed):
+        srv = make()
+        cam = Camera(srv, ring, shapes, n, rate, seed=seed)
+        cam.start()
+        srv.run(cam.expected(), timeout_s=600)
+        cam.join(timeout=60)
+        if cam.error is not None:
+            raise cam.error
+        torch.cuda.synchronize()
+        st = serve_stats(srv, cam.t0)
+        if isinstance(srv, LiveViewServer):
+            st["mean_batch"] = round(float(np.mean(srv.batch_sizes)), 2)
+            st["peak_device_bytes"] = srv.peak_in_use
+        st["ring_stalls"] = ring.stalls
+        return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+
+    makers = {"batched": lambda: LiveViewServer(plans, budget, keep_results=False),
+              "plain": lambda: PlainServer(plans, keep_results=False)}
+    for name, make in makers.items():
+        one(make, None, 16, seed=1)                                   # warm-up: allocators, plans
+        for phase, rate, n in phases:
+            if n > 0:
+                ring.stalls = 0
+                out.setdefault(phase, {"rate_per_s": rate, "stacks": n})[name] = one(make, rate, n, seed=2)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +224,11 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=256)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-paced", type=int, default=200, help="stacks at Poisson arrivals (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-saturated", type=int, default=1800, help="stacks arriving at once (0: skip)")
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--serve-ring-gb", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -310,6 +359,10 @@ def main():
         "gpu_launches": 3 * K,
         "clocks": clocks,
     }
+    if args.serve_paced > 0 or args.serve_saturated > 0:
+        del vol, raw
+        torch.cuda.empty_cache()
+        line["serving"] = serve_bench(args, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(R, cfg, args.ref_cols)
     print(json.dumps(line), flush=True)

@@ -153,3 +153,29 @@ def bright_voxel(shape, n0: int, r0: int, x0: int, value: float = 1.0,
     a = np.zeros(shape, dtype=dtype)
     a[n0, r0, x0] = value
     return a
+
+
+def tiled_stack(shape, seed: int = 5) -> np.ndarray:
+    """uint16 stack of any shape filled by repeating one Poisson+blob tile.
+
+    Content stand-in for the serving workload, where stacks of up to several
+    GB arrive continuously and only their shapes matter for the schedule.
+    """
+    tile = raw_stack(StackConfig("tile", 50, 128, 256, 35.0, 0.3, 0.1, n_blobs=12, sigma=(1.5, 4.0),
+                                 amp=(200.0, 5000.0), seed=seed))
+    reps = [-(-s // t) for s, t in zip(shape, tile.shape)]
+    return np.tile(tile, reps)[: shape[0], : shape[1], : shape[2]]
+
+
+SERVE_ROWS = (256, 512, 1024)
+SERVE_COLS = (512, 1024, 2048)
+
+
+def serve_shapes(n: int, seed: int = 5, planes=(50, 400), channels: int = 2,
+                 rows=SERVE_ROWS, cols=SERVE_COLS):
+    """Seeded request shapes (nscan, nrows, ncols per channel, channels):
+    rows and columns uniform over the given sets, planes uniform over the
+    range in steps of 50, as in a live-imaging session of varying ROIs."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0x5E7])))
+    pl = np.arange(planes[0], planes[1] + 1, 50)
+    return [(int(rng.choice(pl)), int(rng.choice(rows)), int(rng.choice(cols)), channels) for _ in range(n)]

@@ -1,0 +1,545 @@
+"""Live-view serving: camera stacks arrive, live views come back.
+
+The paper refreshes its widefield-like view while the camera keeps
+acquiring, and shows that the lag between acquisition and display grows
+once processing is slower than the camera (Supp. Fig. 1).  This module serves
+that loop on one GPU:
+
+* a producer (camera stand-in) writes each stack into a pinned host ring
+  buffer (``PinnedRing``) and publishes it at its arrival time; when the ring
+  is full the camera stalls (back-pressure) and the stall counts as lag;
+* the scheduler admits a request when its device footprint (raw stack plus
+  outputs) fits a memory budget, copies it to the device on a copy stream and
+  keeps it resident until its views are back on the host;
+* every tick launches one persistent batched projection (``Batch``) over all
+  admitted requests whose copies have landed, channels as strided ROIs of the
+  stack, while later copies and the previous tick's read-back proceed on the
+  copy stream (continuous batching: a request that arrives while a batch runs
+  joins the next tick);
+* a ring range is released as soon as its copy to the device has landed;
+* latency is arrival -> projections in host memory, the paper's lag.
+
+``PlainServer`` is the reference path: one request at a time, synchronous
+copy in, one projection per channel, copy out.
+"""
+from __future__ import annotations
+
+import bisect
+import dataclasses
+import threading
+import time
+from collections import deque
+from typing import Callable, Dict, List, Optional, Tuple
+
+import numpy as np
+
+
+# ------------------------------------------------------------------ arena
+class DeviceArena:
+    """First-fit allocator of byte ranges inside a budget.
+
+    Pure bookkeeping over offsets; ``base`` (a device tensor) is optional so
+    the policy can be exercised without a GPU.  Free ranges are coalesced.
+    """
+
+    def __init__(self, budget: int, align: int = 256, base=None):
+        if budget <= 0:
+            raise ValueError("budget must be positive")
+        self.budget = int(budget)
+        self.align = int(align)
+        self.base = base
+        self._free: List[Tuple[int, int]] = [(0, self.budget)]  # sorted (offset, size)
+        self._used: Dict[int, int] = {}
+
+    def _round(self, n: int) -> int:
+        return (int(n) + self.align - 1) // self.align * self.align
+
+    @property
+    def in_use(self) -> int:
+        return sum(self._used.values())
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        size = self._round(max(1, nbytes))
+        for i, (off, sz) in enumerate(self._free):
+            if sz >= size:
+                if sz == size:
+                    self._free.pop(i)
+                else:
+                    self._free[i] = (off + size, sz - size)
+                self._used[off] = size
+                return off
+        return None
+
+    def free(self, off: int) -> None:
+        size = self._used.pop(off)
+        i = bisect.bisect_left(self._free, (off, 0))
+        self._free.insert(i, (off, size))
+        # coalesce with neighbours
+        if i + 1 < len(self._free) and self._free[i][0] + self._free[i][1] == self._free[i + 1][0]:
+            o, s = self._free.pop(i + 1)
+            self._free[i] = (self._free[i][0], self._free[i][1] + s)
+        if i > 0 and self._free[i - 1][0] + self._free[i - 1][1] == self._free[i][0]:
+            o, s = self._free.pop(i)
+            self._free[i - 1] = (self._free[i - 1][0], self._free[i - 1][1] + s)
+
+    def view(self, off: int, nbytes: int):
+        """uint8 device view of an allocation (needs ``base``)."""
+        return self.base[off:off + nbytes]
+
+
+# ------------------------------------------------------------ pinned ring
+class PinnedRing:
+    """Byte ring of (pinned) host memory that camera stacks are written into.
+
+    Ranges are taken at the head in arrival order and wrap to the start when
+    the tail end is too short; a range is returned when every request that
+    refers to it has released it, and the tail advances over returned ranges
+    in order.  ``acquire`` blocks while the ring is full (back-pressure).
+
+    The content is written once at construction (``fill(uint8_array, seed)``
+    fills it in place; default: repeated Poisson+blob tiles), standing in
+    for the camera's DMA into the ring: a stack published at an offset holds
+    whatever frames the ring has there, which keeps acquisition itself free.
+    """
+
+    def __init__(self, nbytes: int, pin: bool = True, align: int = 256, fill=None, seed: int = 5):
+        import torch
+        self.nbytes = int(nbytes)
+        self.align = int(align)
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=pin)
+        (fill or _tile_fill)(self.buf.numpy(), seed)
+        self._entries: deque = deque()          # [offset, size, refs]
+        self._cond = threading.Condition()
+        self.stalls = 0
+        self.peak = 0
+
+    def _round(self, n: int) -> int:
+        return (int(n) + self.align - 1) // self.align * self.align
+
+    def _place(self, size: int) -> Optional[int]:
+        if not self._entries:
+            return 0 if size <= self.nbytes else None
+        tail = self._entries[0][0]
+        last_off, last_size, _ = self._entries[-1]
+        head = last_off + last_size
+        if last_off >= tail:                    # not wrapped: free space at the end, then before tail
+            if head + size <= self.nbytes:
+                return head
+            return 0 if size <= tail else None
+        return head if head + size <= tail else None
+
+    def in_use(self) -> int:
+        with self._cond:
+            return sum(e[1] for e in self._entries)
+
+    def acquire(self, nbytes: int, refs: int = 1, timeout: Optional[float] = None) -> int:
+        size = self._round(max(1, nbytes))
+        if size > self.nbytes:
+            raise ValueError(f"stack of {nbytes} bytes exceeds the {self.nbytes}-byte ring")
+        t_end = None if timeout is None else time.perf_counter() + timeout
+        with self._cond:
+            stalled = False
+            while True:
+                off = self._place(size)
+                if off is not None:
+                    break
+                if not stalled:
+                    self.stalls += 1
+                    stalled = True
+                left = None if t_end is None else t_end - time.perf_counter()
+                if left is not None and left <= 0:
+                    raise TimeoutError("pinned ring full")
+                self._cond.wait(left if left is not None else 1.0)
+            self._entries.append([off, size, int(refs)])
+            self.peak = max(self.peak, sum(e[1] for e in self._entries))
+            return off
+
+    def release(self, off: int) -> None:
+        with self._cond:
+            for e in self._entries:
+                if e[0] == off and e[2] > 0:
+                    e[2] -= 1
+                    break
+            else:
+                raise KeyError(f"no live ring range at {off}")
+            while self._entries and self._entries[0][2] == 0:
+                self._entries.popleft()
+            self._cond.notify_all()
+
+    def view(self, off: int, shape):
+        """uint16 host tensor of ``shape`` at byte offset ``off``."""
+        import torch
+        n = int(np.prod(shape)) * 2
+        return self.buf[off:off + n].view(torch.uint16).view(*shape)
+
+
+def _tile_fill(out: np.ndarray, seed: int) -> None:
+    """Fills ``out`` in place with repeats of one 50x128x256 stack tile."""
+    import opm_synth
+    tile = opm_synth.tiled_stack((50, 128, 256), seed=seed).view(np.uint8).ravel()
+    k = min(tile.size, out.size)
+    out[:k] = tile[:k]
+    while k < out.size:                       # doubling copies
+        m = min(k, out.size - k)
+        out[k:k + m] = out[:m]
+        k += m
+
+
+# ---------------------------------------------------------------- requests
+@dataclasses.dataclass
+class Request:
+    rid: int
+    nscan: int
+    nrows: int
+    ncols: int            # per channel
+    channels: int
+    host: object          # pinned uint16 tensor [nscan][nrows][channels*ncols]
+    t_arrival: float = 0.0
+    t_done: float = 0.0
+    dropped: bool = False
+    error: Optional[str] = None
+    results: Optional[list] = None   # per channel {"zmip", "ymip"} host tensors
+    ring: Optional[PinnedRing] = None  # ring holding ``host``, released once copied
+    ring_off: int = -1
+
+    def release_host(self) -> None:
+        if self.ring is not None:
+            ring, self.ring = self.ring, None
+            ring.release(self.ring_off)
+
+    @property
+    def shape(self):
+        return (self.nscan, self.nrows, self.ncols)
+
+    @property
+    def latency_ms(self) -> float:
+        return (self.t_done - self.t_arrival) * 1e3
+
+
+def request_bytes(plan, channels: int) -> int:
+    """Device footprint: raw frames of every channel plus z-MIP and y-MIP."""
+    raw = 2 * plan.nscan * plan.nrows * plan.ncols * channels
+    outs = 4 * (plan.ny * plan.nx + plan.nz * plan.nx) * channels
+    return raw + outs + (1 + 2 * channels) * 256  # one 256-byte alignment gap per sub-buffer
+
+
+def percentile(xs, q):
+    if not xs:
+        return None
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+class PlanCache:
+    """One plan per stack shape for a fixed sheet angle, scan step and pixel."""
+
+    def __init__(self, theta_deg: float, step: float, pixel: float):
+        self.theta_deg, self.step, self.pixel = float(theta_deg), float(step), float(pixel)
+        self._plans: Dict[Tuple[int, int, int], object] = {}
+
+    def get(self, nscan: int, nrows: int, ncols: int):
+        from . import Plan
+        key = (int(nscan), int(nrows), int(ncols))
+        if key not in self._plans:
+            self._plans[key] = Plan(*key, self.theta_deg, self.step, self.pixel)
+        return self._plans[key]
+
+
+class _Resident:
+    """A request admitted to the device: arena range, device views, events."""
+
+    def __init__(self, req: Request, plan, off: int, arena: DeviceArena, torch):
+        self.req, self.plan, self.off = req, plan, off
+        C = req.channels
+        nraw = 2 * plan.nscan * plan.nrows * plan.ncols * C
+        pos = off
+        self.raw = arena.view(pos, nraw).view(torch.uint16).view(plan.nscan, plan.nrows, plan.ncols * C)
+        pos += (nraw + 255) // 256 * 256
+        self.z, self.y = [], []
+        for _ in range(C):
+            nz = 4 * plan.ny * plan.nx
+            self.z.append(arena.view(pos, nz).view(torch.float32).view(plan.ny, plan.nx))
+            pos += (nz + 255) // 256 * 256
+            ny = 4 * plan.nz * plan.nx
+            self.y.append(arena.view(pos, ny).view(torch.float32).view(plan.nz, plan.nx))
+            pos += (ny + 255) // 256 * 256
+        self.h2d = None
+        self.launched = False
+
+
+class LiveViewServer:
+    """Continuous-batching live-view server on one GPU (see module docstring)."""
+
+    def __init__(self, plans: PlanCache, budget_bytes: int, max_items: int = 256, max_units: int = 1 << 22,
+                 kchunk: int = 0, ctas_per_sm: int = 0, max_inflight: int = 2, keep_results: bool = True):
+        import torch
+
+        from . import Batch
+        self.torch = torch
+        self.plans = plans
+        self.arena = DeviceArena(budget_bytes, base=torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda"))
+        self.h2d = torch.cuda.Stream()
+        self.d2h = torch.cuda.Stream()
+        self.comp = torch.cuda.Stream()
+        self.batches = [Batch(max_items, max_units) for _ in range(max_inflight)]
+        self.max_items = max_items
+        self.kchunk, self.ctas = kchunk, ctas_per_sm
+        self.max_inflight = max_inflight
+        self.keep_results = keep_results
+        self._lock = threading.Lock()
+        self._arrivals: deque = deque()
+        self.waiting: deque = deque()
+        self.resident: List[_Resident] = []
+        self.inflight: deque = deque()
+        self.done: List[Request] = []
+        self.rejected: List[Request] = []
+        self.peak_in_use = 0
+        self.ticks = 0
+        self.batch_sizes: List[int] = []
+
+    # producer side ------------------------------------------------------
+    def submit(self, req: Request) -> None:
+        with self._lock:
+            self._arrivals.append(req)
+
+    # scheduler ----------------------------------------------------------
+    def _admit(self) -> None:
+        torch = self.torch
+        with self._lock:
+            while self._arrivals:
+                self.waiting.append(self._arrivals.popleft())
+        while self.waiting:
+            req = self.waiting[0]
+            plan = self.plans.get(req.nscan, req.nrows, req.ncols)
+            need = request_bytes(plan, req.channels)
+            if need > self.arena.budget:       # can never fit: refuse, keep serving others
+                self.waiting.popleft()
+                req.error = f"needs {need} bytes, budget {self.arena.budget}"
+                req.t_done = time.perf_counter()
+                self.rejected.append(req)
+                req.release_host()
+                continue
+            off = self.arena.alloc(need)
+            if off is None:                    # wait for memory (FIFO, no overtaking)
+                break
+            self.waiting.popleft()
+            r = _Resident(req, plan, off, self.arena, torch)
+            with torch.cuda.stream(self.h2d):
+                r.raw.view(torch.int16).copy_(req.host.view(torch.int16), non_blocking=True)
+                r.h2d = torch.cuda.Event()
+                r.h2d.record(self.h2d)
+            self.resident.append(r)
+            self.peak_in_use = max(self.peak_in_use, self.arena.in_use)
+
+    def _launch_tick(self) -> bool:
+        torch = self.torch
+        if len(self.inflight) >= self.max_inflight:
+            return False
+        ready = []
+        nitems = 0
+        full = False
+        for r in self.resident:
+            if r.launched or not r.h2d.query():
+                continue
+            r.req.release_host()                 # copy landed: the ring range is free
+            if full or nitems + r.req.channels > self.max_items:
+                full = True                      # keep arrival order: later requests wait too
+                continue
+            ready.append(r)
+            nitems += r.req.channels
+        if not ready:
+            return False
+        b = self.batches[self.ticks % len(self.batches)]
+        items = []
+        for r in ready:
+            C, n = r.req.channels, r.plan.ncols
+            for c in range(C):
+                items.append({"plan": r.plan, "raw": r.raw[:, :, c * n:], "row_pitch": C * n,
+                              "plane_pitch": r.plan.nrows * C * n, "zmip": r.z[c], "ymip": r.y[c]})
+        b.set(items, self.kchunk)
+        for r in ready:
+            self.comp.wait_event(r.h2d)
+            r.launched = True
+        b.upload(self.comp)
+        b.launch(self.ctas, self.comp)
+        ev_c = torch.cuda.Event()
+        ev_c.record(self.comp)
+        self.d2h.wait_event(ev_c)
+        with torch.cuda.stream(self.d2h):
+            for r in ready:
+                res = []
+                for c in range(r.req.channels):
+                    hz = torch.empty(r.z[c].shape, dtype=torch.float32, pin_memory=True)
+                    hy = torch.empty(r.y[c].shape, dtype=torch.float32, pin_memory=True)
+                    hz.copy_(r.z[c], non_blocking=True)
+                    hy.copy_(r.y[c], non_blocking=True)
+                    res.append({"zmip": hz, "ymip": hy})
+                r.req.results = res
+            ev_d = torch.cuda.Event()
+            ev_d.record(self.d2h)
+        self.inflight.append((ready, ev_d))
+        self.ticks += 1
+        self.batch_sizes.append(len(ready))
+        return True
+
+    def _retire(self, block: bool) -> bool:
+        if not self.inflight:
+            return False
+        ready, ev_d = self.inflight[0]
+        if block:
+            ev_d.synchronize()
+        elif not ev_d.query():
+            return False
+        t = time.perf_counter()
+        self.inflight.popleft()
+        for r in ready:
+            r.req.t_done = t
+            if not self.keep_results:
+                r.req.results = None
+            self.arena.free(r.off)
+            self.resident.remove(r)
+            self.done.append(r.req)
+        return True
+
+    def step(self) -> None:
+        """One scheduler pass: admit, launch a tick, retire finished ticks."""
+        self._admit()
+        launched = self._launch_tick()
+        retired = self._retire(block=False)
+        if not launched and not retired and self.inflight:
+            # nothing else to do: wait for the oldest tick (frees memory too)
+            self._retire(block=True)
+
+    def run(self, n_expected: int, timeout_s: float = 600.0, idle=None) -> None:
+        t_end = time.perf_counter() + timeout_s
+        while len(self.done) + len(self.rejected) < n_expected:
+            if time.perf_counter() > t_end:
+                raise TimeoutError(f"served {len(self.done)} of {n_expected} requests")
+            self.step()
+            if not self.inflight and not self.resident and not self.waiting:
+                with self._lock:
+                    empty = not self._arrivals
+                if empty:
+                    time.sleep(idle if idle is not None else 0.0002)
+
+
+class PlainServer:
+    """Reference path: one request at a time on one stream, synchronous copy
+    in, one stand-alone projection per channel, copy out."""
+
+    def __init__(self, plans: PlanCache, keep_results: bool = True):
+        import torch
+        self.torch = torch
+        self.plans = plans
+        self.keep_results = keep_results
+        self._lock = threading.Lock()
+        self._arrivals: deque = deque()
+        self.done: List[Request] = []
+        self.rejected: List[Request] = []
+
+    def submit(self, req: Request) -> None:
+        with self._lock:
+            self._arrivals.append(req)
+
+    def _serve(self, req: Request) -> None:
+        from . import opm_project
+        torch = self.torch
+        plan = self.plans.get(req.nscan, req.nrows, req.ncols)
+        raw = torch.empty(req.host.shape, dtype=torch.uint16, device="cuda")
+        raw.view(torch.int16).copy_(req.host.view(torch.int16))
+        req.release_host()
+        res = []
+        n = req.ncols
+        for c in range(req.channels):
+            ch = raw[:, :, c * n:(c + 1) * n].contiguous()
+            z = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device="cuda")
+            y = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device="cuda")
+            opm_project(plan, ch, z, None, y, None)
+            res.append({"zmip": z.cpu(), "ymip": y.cpu()})
+        torch.cuda.synchronize()
+        req.results = res if self.keep_results else None
+        req.t_done = time.perf_counter()
+        self.done.append(req)
+
+    def run(self, n_expected: int, timeout_s: float = 600.0, idle=None) -> None:
+        t_end = time.perf_counter() + timeout_s
+        while len(self.done) + len(self.rejected) < n_expected:
+            if time.perf_counter() > t_end:
+                raise TimeoutError(f"served {len(self.done)} of {n_expected} requests")
+            with self._lock:
+                req = self._arrivals.popleft() if self._arrivals else None
+            if req is None:
+                time.sleep(idle if idle is not None else 0.0002)
+                continue
+            self._serve(req)
+
+
+class Camera(threading.Thread):
+    """Camera stand-in: writes stacks into a pinned ring and publishes them at
+    Poisson arrival times.
+
+    ``shapes`` lists request shapes (nscan, nrows, ncols per channel,
+    channels); arrival i takes ``shapes[order[i]]`` with a seeded order.
+    ``rate`` stacks/s (None: all at once, saturating).  A request's arrival
+    time is its scheduled time, so a stall on a full ring counts as lag.
+    Host-side fault injection for tests: ``drop`` (arrival indices never
+    delivered), ``duplicate`` (delivered twice, sharing one ring range) and
+    ``delay_s`` (extra delay per index).
+    """
+
+    def __init__(self, server, ring: PinnedRing, shapes, n: int, rate: Optional[float], seed: int = 0,
+                 drop=(), duplicate=(), delay_s=None, ring_timeout: float = 120.0):
+        super().__init__(daemon=True)
+        self.server, self.ring, self.shapes, self.n, self.rate = server, ring, list(shapes), n, rate
+        rng = np.random.default_rng(seed)
+        self.order = rng.integers(0, len(self.shapes), n)
+        gaps = rng.exponential(1.0 / rate, n) if rate else np.zeros(n)
+        self.offsets = np.cumsum(gaps) - (gaps[0] if n else 0.0)
+        self.drop, self.duplicate = set(drop), set(duplicate)
+        self.delay_s = dict(delay_s or {})
+        self.ring_timeout = ring_timeout
+        self.delivered = 0
+        self.error: Optional[BaseException] = None
+        self.t0 = None
+
+    def expected(self) -> int:
+        return self.n - len([i for i in self.drop if i < self.n]) + len([i for i in self.duplicate if i < self.n])
+
+    def run(self) -> None:
+        try:
+            self._run()
+        except BaseException as e:        # surfaced by the caller through ``error``
+            self.error = e
+
+    def _run(self) -> None:
+        self.t0 = time.perf_counter()
+        rid = 0
+        for i in range(self.n):
+            t = self.t0 + self.offsets[i] + self.delay_s.get(i, 0.0)
+            while True:
+                now = time.perf_counter()
+                if now >= t:
+                    break
+                time.sleep(min(t - now, 0.001))
+            if i in self.drop:
+                continue
+            nscan, nrows, ncols, C = self.shapes[int(self.order[i])]
+            shape = (nscan, nrows, ncols * C)
+            copies = 2 if i in self.duplicate else 1
+            off = self.ring.acquire(2 * nscan * nrows * ncols * C, refs=copies, timeout=self.ring_timeout)
+            host = self.ring.view(off, shape)
+            for _ in range(copies):
+                self.server.submit(Request(rid, nscan, nrows, ncols, C, host, t_arrival=t, ring=self.ring,
+                                           ring_off=off))
+                rid += 1
+                self.delivered += 1
+
+
+def serve_stats(server, t_first: float) -> dict:
+    lat = [r.latency_ms for r in server.done]
+    t_last = max((r.t_done for r in server.done), default=t_first)
+    span = max(t_last - t_first, 1e-9)
+    ch = sum(r.channels for r in server.done)
+    return {"served": len(server.done), "rejected": len(server.rejected),
+            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "max_ms": max(lat) if lat else None,
+            "stacks_per_s": len(server.done) / span, "volumes_per_s": ch / span, "span_s": span}
+

@@ -207,6 +207,41 @@ opm_status opm_batch_check(const opm_batch* b);
 opm_status opm_batch_destroy(opm_batch* b);
 
 /*
+ * opm_batch_project_static - the batched live view (opm_batch_set, upload
+ * and launch in one call, same kernels and results) with nothing allocated:
+ * the work list is built in a fixed host array and copied into a fixed
+ * device array reserved when the library is loaded (about 2.1 MB per
+ * device).  The paper has no counterpart to this call.
+ *
+ * Why: cudaMalloc and cudaFree can synchronise the whole device and take
+ * milliseconds, which stalls the copy and compute streams of a live
+ * acquisition; a caller with a hard per-frame deadline, or one that accounts
+ * for every device byte before it starts (a fixed memory plan), cannot
+ * create an opm_batch on the fly.  This call gives it a fixed footprint.
+ *
+ * Limits: at most 64 items and 65536 work units per call (a unit is one
+ * 32-column j-tile x 128-column x-tile x kchunk rows of one item); larger
+ * requests fail with OPM_ERR_UNSUPPORTED and launch nothing.  Item rules as
+ * for opm_batch_set.  kchunk: rows per unit (0: 64); ctas_per_sm: 1..4 (0: 4).
+ * check != 0 synchronises cuda_stream afterwards and reports a failed
+ * device consistency check as OPM_ERR_INTERNAL (a diagnostic, not for the
+ * hot path).
+ *
+ * The first call on each device does set-up (looks up the device array's
+ * address with that device current, sets the kernel's shared-memory limit);
+ * make it before any stream capture.  The host array is copied with
+ * pageable cudaMemcpyAsync, which returns once the data is staged, so the
+ * call blocks for prior work on cuda_stream.  There is one host array and
+ * one device array per device: calls that overlap, from several threads or
+ * on several streams of one device, race and corrupt each other's work
+ * lists; serialise them (consecutive calls on one stream are safe).
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED, OPM_ERR_CUDA,
+ * OPM_ERR_INTERNAL (check only).
+ */
+opm_status opm_batch_project_static(const opm_batch_item* items, int n_items, int kchunk, int ctas_per_sm,
+                                    int check, void* cuda_stream);
+
+/*
  * opm_plan_check - synchronising diagnostic (not for the hot path): waits for
  * the plan's device, then reports OPM_ERR_INTERNAL if any kernel launched with
  * this plan recorded a failed internal consistency check (and clears the

@@ -59,6 +59,8 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int)]),
     "opm_batch_check": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "opm_batch_project_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_void_p]),
     "opm_last_error": (ctypes.c_char_p, []),
     "opm_version": (ctypes.c_int, []),
 }
@@ -264,6 +266,26 @@ def mip_backward(plan: Plan, g_zmip, argz, stream=None):
 
 
 # ----------------------------------------------------------------- batches
+def batch_project_static(items, kchunk: int = 0, ctas_per_sm: int = 0, check: bool = False, stream=None):
+    """``opm_batch_project_static``: the batched live view of ``items`` (dicts
+    as for ``Batch.set``) in one call that allocates no device memory, for
+    callers that must not allocate (a fixed memory plan, a per-frame
+    deadline).  At most 64 items and 65536 work units; calls that overlap on
+    one device race."""
+    arr = (opm_batch_item * max(1, len(items)))()
+    for i, it in enumerate(items):
+        raw = it["raw"]
+        if not raw.is_cuda:
+            raise ValueError("raw must be a CUDA tensor")
+        z, y = it.get("zmip"), it.get("ymip")
+        arr[i] = opm_batch_item(it["plan"].handle.value, raw.data_ptr(), int(it.get("row_pitch", 0)),
+                                int(it.get("plane_pitch", 0)), z.data_ptr() if z is not None else None,
+                                y.data_ptr() if y is not None else None)
+    _check(load().opm_batch_project_static(ctypes.cast(arr, ctypes.c_void_p), len(items), int(kchunk),
+                                           int(ctas_per_sm), int(bool(check)), _stream(stream)),
+           "opm_batch_project_static")
+
+
 class Batch:
     """Owns an ``opm_batch*``: one persistent launch of the fused z-MIP/y-MIP
     over many uint16 stacks, channels (strided ROIs) and ROIs."""

@@ -329,3 +329,196 @@ opm_status opm_batch_check(const opm_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched live view.
+//
+// Same kernels and arithmetic as the opm_batch_* path, but the work list
+// lives in a fixed file-scope device array instead of memory allocated per
+// batch: at most kStaticItems items and kStaticUnits work units, about 2.1 MB
+// of device memory reserved when the library is loaded.  The host side
+// builds the list in a fixed host array of the same layout, so a successful
+// call makes no allocation of any kind.
+namespace opm {
+namespace {
+
+constexpr int kStaticItems = 64;
+constexpr int64_t kStaticUnits = 1 << 16;
+constexpr int kStaticDevices = 64;
+constexpr size_t cal256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kSOffUnits = cal256(sizeof(BatchItemDev) * kStaticItems);
+constexpr size_t kSOffSegs = kSOffUnits + cal256(sizeof(BatchUnit) * kStaticUnits);
+constexpr size_t kSOffErr = kSOffSegs + cal256(sizeof(BatchSeg) * 2 * kStaticItems);
+constexpr size_t kSBytes = kSOffErr + 256;
+
+struct StaticDevice {
+  bool ready;
+  unsigned char* scratch;  // device address of the static array on this device
+  int nsm, smem_optin;
+};
+
+alignas(256) unsigned char g_static_stage[kSBytes];  // host image of the work list
+StaticDevice g_static_dev[kStaticDevices];
+std::mutex g_static_mu;
+
+bool unit_before(const BatchUnit& a, const BatchUnit& c) {
+  // longest first; ties in generation order (item, j-tile, chunk, x-tile),
+  // the order the batch path's stable sort keeps
+  const int la = a.ke - a.ks, lc = c.ke - c.ks;
+  if (la != lc) return la > lc;
+  if (a.item != c.item) return a.item < c.item;
+  if (a.jt != c.jt) return a.jt < c.jt;
+  if (a.ks != c.ks) return a.ks < c.ks;
+  return a.xt < c.xt;
+}
+
+}  // namespace
+}  // namespace opm
+
+static __device__ __align__(256) unsigned char g_static_scratch[opm::kSBytes];
+
+namespace opm {
+namespace {
+
+opm_status static_setup(int dev, StaticDevice** out) {
+  if (dev < 0 || dev >= kStaticDevices)
+    return fail(OPM_ERR_UNSUPPORTED, "device ordinal " + std::to_string(dev) + " beyond the static table");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticDevice& d = g_static_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static set-up");
+    if ((uintptr_t)p % 256 != 0) return fail(OPM_ERR_INTERNAL, "static scratch is not 256-byte aligned");
+    d.scratch = static_cast<unsigned char*>(p);
+    d.ready = true;
+  }
+  *out = &d;
+  return OPM_OK;
+}
+
+}  // namespace
+}  // namespace opm
+
+extern "C" opm_status opm_batch_project_static(const opm_batch_item* items, int n_items, int kchunk,
+                                               int ctas_per_sm, int check, void* stream) {
+  if (!items && n_items > 0) return fail(OPM_ERR_INVALID_ARG, "items is NULL");
+  if (n_items < 0) return fail(OPM_ERR_INVALID_ARG, "n_items must be >= 0");
+  if (n_items > kStaticItems)
+    return fail(OPM_ERR_UNSUPPORTED, std::to_string(n_items) + " items exceed the static limit of " +
+                                         std::to_string(kStaticItems));
+  if (kchunk < 0) return fail(OPM_ERR_INVALID_ARG, "kchunk must be >= 0");
+  if (ctas_per_sm < 0 || ctas_per_sm > 4) return fail(OPM_ERR_INVALID_ARG, "ctas_per_sm must lie in [0, 4]");
+  if (kchunk == 0) kchunk = 64;
+  if (ctas_per_sm == 0) ctas_per_sm = 4;
+  if (!batch_encode_fn()) return fail(OPM_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is unavailable");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  StaticDevice* sd = nullptr;
+  opm_status st = static_setup(dev, &sd);
+  if (st != OPM_OK) return st;
+
+  BatchItemDev* hitems = reinterpret_cast<BatchItemDev*>(g_static_stage);
+  BatchUnit* hunits = reinterpret_cast<BatchUnit*>(g_static_stage + kSOffUnits);
+  BatchSeg* hsegs = reinterpret_cast<BatchSeg*>(g_static_stage + kSOffSegs);
+  int64_t nunits = 0;
+  int Pl = 2, nseg = 0;
+  for (int i = 0; i < n_items; ++i) {
+    const opm_batch_item& it = items[i];
+    const opm_plan* p = it.plan;
+    if (!p || !it.raw) return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": NULL plan or raw");
+    if (p->device != dev) return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) + ": plan on another device");
+    if (!plan_fast_ok(p))
+      return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
+                                           ": plan not eligible (needs pixel <= step and ny >= 32)");
+    const int64_t rp = it.row_pitch ? it.row_pitch : p->ncols;
+    const int64_t pp = it.plane_pitch ? it.plane_pitch : p->nrows * rp;
+    if (rp < p->ncols || pp < p->nrows * rp)
+      return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": pitches smaller than the ROI");
+    if ((uintptr_t)it.raw % 16 != 0 || rp % 8 != 0 || pp % 8 != 0)
+      return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
+                                           ": raw must be 16-byte aligned and pitches multiples of 8 elements");
+    BatchItemDev& d = hitems[i];
+    std::memset(&d, 0, sizeof(d));
+    const cuuint64_t dims[3] = {(cuuint64_t)p->ncols, (cuuint64_t)p->nrows, (cuuint64_t)p->nscan};
+    const cuuint64_t strides[2] = {(cuuint64_t)rp * 2, (cuuint64_t)pp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kX, 1u, (cuuint32_t)p->P};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult cr = batch_encode_fn()(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t*>(it.raw), dims,
+                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS)
+      return fail(OPM_ERR_CUDA, "item " + std::to_string(i) + ": cuTensorMapEncodeTiled failed (" +
+                                    std::to_string((int)cr) + ")");
+    d.frow = p->view.frow;
+    d.fnlo = p->view.fnlo;
+    d.zmip = it.zmip;
+    d.ymip = it.ymip;
+    d.nz = (int)p->nz;
+    d.ny = (int)p->ny;
+    d.nx = (int)p->nx;
+    d.P = p->P;
+    Pl = std::max(Pl, p->P);
+    if (it.zmip) hsegs[nseg++] = BatchSeg{it.zmip, (long long)(p->ny * p->nx)};
+    if (it.ymip) hsegs[nseg++] = BatchSeg{it.ymip, (long long)(p->nz * p->nx)};
+    if (!it.zmip && !it.ymip) continue;
+    const int xtiles = (int)((p->nx + kX - 1) / kX);
+    const int jtiles = (int)((p->ny + kTileJ - 1) / kTileJ);
+    for (int jt = 0; jt < jtiles; ++jt) {
+      const Band bd = p->hBand[jt];
+      for (int c0 = (bd.lo / kchunk) * kchunk; c0 < bd.hi; c0 += kchunk) {
+        const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + kchunk);
+        if (ks >= ke) continue;
+        if (nunits + xtiles > kStaticUnits)
+          return fail(OPM_ERR_UNSUPPORTED, "the items need more than the static limit of " +
+                                               std::to_string(kStaticUnits) + " work units (raise kchunk or split)");
+        for (int xt = 0; xt < xtiles; ++xt) hunits[nunits++] = BatchUnit{i, xt, jt, ks, ke, {0, 0, 0}};
+      }
+    }
+  }
+  std::sort(hunits, hunits + nunits, unit_before);
+
+  // Pageable host -> device copies: each returns once its source has been
+  // staged, so the host image may be rebuilt by the next call.
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* dv = sd->scratch;
+  if (n_items > 0) e = cudaMemcpyAsync(dv, g_static_stage, sizeof(BatchItemDev) * n_items, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nunits > 0)
+    e = cudaMemcpyAsync(dv + kSOffUnits, g_static_stage + kSOffUnits, sizeof(BatchUnit) * nunits,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nseg > 0)
+    e = cudaMemcpyAsync(dv + kSOffSegs, g_static_stage + kSOffSegs, sizeof(BatchSeg) * nseg, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dv + kSOffErr, 0, sizeof(unsigned), s);  // error word starts at 0
+  if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static upload");
+  if (nseg > 0) {
+    dim3 grid(64, std::min(nseg, 65535));
+    k_batch_zero<<<grid, 256, 0, s>>>(reinterpret_cast<const BatchSeg*>(dv + kSOffSegs), nseg);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_batch_zero");
+  }
+  if (nunits > 0) {
+    const size_t smem = fast::total(Pl);
+    if ((int)smem > sd->smem_optin) return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
+    const int grid = (int)std::min<int64_t>(nunits, (int64_t)sd->nsm * ctas_per_sm);
+    k_batch_fast<<<grid, kThreads, smem, s>>>(reinterpret_cast<const BatchItemDev*>(dv),
+                                              reinterpret_cast<const BatchUnit*>(dv + kSOffUnits), (int)nunits, Pl,
+                                              reinterpret_cast<unsigned*>(dv + kSOffErr));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_batch_fast");
+  }
+  if (check) {
+    unsigned word = 0;
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&word, dv + kSOffErr, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static check");
+    if (word) return fail(OPM_ERR_INTERNAL, "device consistency check failed (bits " + std::to_string(word) + ")");
+  }
+  return OPM_OK;
+}

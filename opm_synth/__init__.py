@@ -164,7 +164,7 @@ def tiled_stack(shape, seed: int = 5) -> np.ndarray:
     tile = raw_stack(StackConfig("tile", 50, 128, 256, 35.0, 0.3, 0.1, n_blobs=12, sigma=(1.5, 4.0),
                                  amp=(200.0, 5000.0), seed=seed))
     reps = [-(-s // t) for s, t in zip(shape, tile.shape)]
-    return np.tile(tile, reps)[: shape[0], : shape[1], : shape[2]]
+    return np.ascontiguousarray(np.tile(tile, reps)[: shape[0], : shape[1], : shape[2]])
 
 
 SERVE_ROWS = (256, 512, 1024)

@@ -202,12 +202,15 @@ __device__ __forceinline__ void stream_step(Stream& st, const unsigned char* lan
 // Streaming on 32-bit shared-memory offsets for the fast kernel (uint16
 // slab): besides the pair (a, d) the lane keeps the raw words of the next
 // plane, loaded right after each step, so that a step converts data already
-// in registers instead of waiting for a shared-memory load.
+// in registers instead of waiting for a shared-memory load.  `nxo` is the
+// offset of those words (plane o + 2).  It may point one plane past the
+// row's slab: the ring is followed by its tables, so the load stays inside
+// the CTA's shared memory, and a plane past the slab is never stepped onto.
 struct StreamPF {
   f2 a[2];
   f2 d[2];
-  uint2 nxt;  // raw words of plane o + 2
-  int o;
+  uint2 nxt;     // raw words of plane o + 2
+  uint32_t nxo;  // their shared-memory offset
 };
 
 __device__ __forceinline__ void lds_row_u16(const unsigned char* smem, uint32_t off, f2 (&out)[2]) {
@@ -217,23 +220,23 @@ __device__ __forceinline__ void lds_row_u16(const unsigned char* smem, uint32_t 
 }
 
 __device__ __forceinline__ void stream_reset_u16(StreamPF& st, const unsigned char* smem, uint32_t lane_off,
-                                                 uint32_t pitch, int o, int P) {
+                                                 uint32_t pitch, int o) {
   f2 b[2];
-  st.o = o;
-  lds_row_u16(smem, lane_off + o * pitch, st.a);
-  lds_row_u16(smem, lane_off + (o + 1) * pitch, b);
-  st.nxt = *reinterpret_cast<const uint2*>(smem + lane_off + min(o + 2, P - 1) * pitch);
+  const uint32_t off = lane_off + (uint32_t)o * pitch;
+  lds_row_u16(smem, off, st.a);
+  lds_row_u16(smem, off + pitch, b);
+  st.nxo = off + 2 * pitch;
+  st.nxt = *reinterpret_cast<const uint2*>(smem + st.nxo);
   st.d[0] = sub2(b[0], st.a[0]);
   st.d[1] = sub2(b[1], st.a[1]);
 }
 
-__device__ __forceinline__ void stream_step_u16(StreamPF& st, const unsigned char* smem, uint32_t lane_off,
-                                                uint32_t pitch, int P) {
+__device__ __forceinline__ void stream_step_u16(StreamPF& st, const unsigned char* smem, uint32_t pitch) {
   f2 b[2];
   b[0] = u16x2_to_f2(st.nxt.x);
   b[1] = u16x2_to_f2(st.nxt.y);
-  st.o += 1;
-  st.nxt = *reinterpret_cast<const uint2*>(smem + lane_off + min(st.o + 2, P - 1) * pitch);
+  st.nxo += pitch;
+  st.nxt = *reinterpret_cast<const uint2*>(smem + st.nxo);
   // integers below 2^24: a + (b - a) == b exactly
   st.a[0] = add2(st.a[0], st.d[0]);
   st.a[1] = add2(st.a[1], st.d[1]);
@@ -257,7 +260,8 @@ __host__ __device__ inline size_t stage_slab_bytes(int P) { return 2 * slab_row_
 __host__ __device__ inline size_t off_tab(int P) { return S * stage_slab_bytes(P); }        // FastRow [S][2]
 __host__ __device__ inline size_t off_ybuf(int P) { return off_tab(P) + S * 2 * sizeof(FastRow); }  // float [S][2][kX]
 __host__ __device__ inline size_t off_bar(int P) { return off_ybuf(P) + S * 2 * kX * 4; }
-__host__ __device__ inline size_t total(int P) { return off_bar(P) + 3 * S * 8; }
+__host__ __device__ inline size_t off_jobs(int P) { return off_bar(P) + 3 * S * 8; }  // JobS [kNW]
+__host__ __device__ inline size_t total(int P) { return off_jobs(P) + kNW * 48; }
 
 }  // namespace fast
 
@@ -280,26 +284,40 @@ struct FastJob {
   int nz, nx, j0, xbase, ks, ke, P;
 };
 
+// A compute warp's job fields that are only needed at the end of a stage or
+// of the job.  They are parked in shared memory and re-read there, so that
+// they hold no registers through the column loop.
+struct JobS {
+  float* zmip;
+  float* ymip;
+  int nx, nz, j0, xbase;
+  int k0g;   // camera row of stage g is k0g + 2 g
+  int gend;  // stage count at the end of the job
+  int pad[2];
+};
+static_assert(sizeof(JobS) == 48, "JobS layout");
+
 // The ring in shared memory, laid out for slab depth Pl (>= every job's P).
+// Region addresses are recomputed from the base on use rather than held in
+// registers.
 struct FastRing {
   unsigned char* base;
-  FastRow* tab;
-  float* ybuf;
-  uint64_t* full;   // producer -> consumers: slabs and tables landed
-  uint64_t* ydone;  // consumers -> producer: slot free
-  uint64_t* cdone;  // consumers -> consumers: y-max of the stage combined
   int Pl;
+  __device__ __forceinline__ FastRow* tab() const { return reinterpret_cast<FastRow*>(base + fast::off_tab(Pl)); }
+  __device__ __forceinline__ float* ybuf() const { return reinterpret_cast<float*>(base + fast::off_ybuf(Pl)); }
+  // producer -> consumers: slabs and tables landed
+  __device__ __forceinline__ uint64_t* full() const { return reinterpret_cast<uint64_t*>(base + fast::off_bar(Pl)); }
+  // consumers -> producer: slot free
+  __device__ __forceinline__ uint64_t* ydone() const { return full() + fast::S; }
+  // consumers -> consumers: y-max of the stage combined
+  __device__ __forceinline__ uint64_t* cdone() const { return full() + 2 * fast::S; }
+  // one per compute warp
+  __device__ __forceinline__ JobS* jobs() const { return reinterpret_cast<JobS*>(base + fast::off_jobs(Pl)); }
 };
 
 __device__ __forceinline__ FastRing fast_ring(unsigned char* smem, int Pl) {
-  using namespace fast;
   FastRing r;
   r.base = smem;
-  r.tab = reinterpret_cast<FastRow*>(smem + off_tab(Pl));
-  r.ybuf = reinterpret_cast<float*>(smem + off_ybuf(Pl));
-  r.full = reinterpret_cast<uint64_t*>(smem + off_bar(Pl));
-  r.ydone = r.full + S;
-  r.cdone = r.full + 2 * S;
   r.Pl = Pl;
   return r;
 }
@@ -309,13 +327,13 @@ __device__ __forceinline__ void fast_ring_init(const FastRing& r) {
   using namespace fast;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(&r.full[s], 1);
-      mbar_init(&r.ydone[s], kNW);
-      mbar_init(&r.cdone[s], kNW);
+      mbar_init(&r.full()[s], 1);
+      mbar_init(&r.ydone()[s], kNW);
+      mbar_init(&r.cdone()[s], kNW);
     }
     fence_barrier_init();
   }
-  for (int i = threadIdx.x; i < S * 2 * kX; i += blockDim.x) r.ybuf[i] = 0.0f;
+  for (int i = threadIdx.x; i < S * 2 * kX; i += blockDim.x) r.ybuf()[i] = 0.0f;
   __syncthreads();
 }
 
@@ -332,7 +350,7 @@ __device__ __forceinline__ bool fast_produce(const FastJob& jb, const FastRing& 
 #pragma unroll 1
   for (int it = 0; it < nst; ++it, ++g) {
     const int s = g % S;
-    if (g >= S && !mbar_wait(&r.ydone[s], ((g - S) / S) & 1, err)) return false;
+    if (g >= S && !mbar_wait(&r.ydone()[s], ((g - S) / S) & 1, err)) return false;
     int nlo[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -348,11 +366,11 @@ __device__ __forceinline__ bool fast_produce(const FastJob& jb, const FastRing& 
       const int k0 = jb.ks + 2 * it;
       const int k1 = k0 + 1;  // k1 == nz: a padding row, staged as TMA zero fill
       unsigned char* slab = r.base + s * stage_slab_bytes(r.Pl);
-      mbar_arrive_tx(&r.full[s], (unsigned)(2 * jb.P * pitch + 2 * sizeof(FastRow)));
-      tma_load_3d(slab, jb.tmap, &r.full[s], jb.xbase, k0, nlo[0]);
-      tma_load_3d(slab + slab_row_bytes(r.Pl), jb.tmap, &r.full[s], jb.xbase, k1, k1 < jb.nz ? nlo[1] : 0);
-      bulk_load(&r.tab[s * 2 + 0], jb.rows + k0, sizeof(FastRow), &r.full[s]);
-      bulk_load(&r.tab[s * 2 + 1], jb.rows + min(k1, jb.nz - 1), sizeof(FastRow), &r.full[s]);
+      mbar_arrive_tx(&r.full()[s], (unsigned)(2 * jb.P * pitch + 2 * sizeof(FastRow)));
+      tma_load_3d(slab, jb.tmap, &r.full()[s], jb.xbase, k0, nlo[0]);
+      tma_load_3d(slab + slab_row_bytes(r.Pl), jb.tmap, &r.full()[s], jb.xbase, k1, k1 < jb.nz ? nlo[1] : 0);
+      bulk_load(&r.tab()[s * 2 + 0], jb.rows + k0, sizeof(FastRow), &r.full()[s]);
+      bulk_load(&r.tab()[s * 2 + 1], jb.rows + min(k1, jb.nz - 1), sizeof(FastRow), &r.full()[s]);
     }
     __syncwarp();
   }
@@ -364,7 +382,19 @@ __device__ __forceinline__ bool fast_produce(const FastJob& jb, const FastRing& 
 __device__ __forceinline__ void fast_drain(const FastRing& r, int g, bool ok, unsigned* err) {
   using namespace fast;
   for (int q = max(0, g - S); q < g; ++q)
-    if (!mbar_wait(&r.full[q % S], (q / S) & 1, err, ok ? kWaitLimitNs : 50000000ull)) break;
+    if (!mbar_wait(&r.full()[q % S], (q / S) & 1, err, ok ? kWaitLimitNs : 50000000ull)) break;
+}
+
+__device__ __forceinline__ int lds_volatile_s32(const int* p) {
+  int v;
+  asm volatile("ld.volatile.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)));
+  return v;
+}
+
+__device__ __forceinline__ float* lds_volatile_ptr(float* const* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(smem_u32(p)));
+  return reinterpret_cast<float*>(v);
 }
 
 // Compute warp cw (0..3): columns j0 + 8cw .. + 7 of the job, both rows of
@@ -375,8 +405,19 @@ __device__ __forceinline__ bool fast_consume(const FastJob& jb, const FastRing& 
                                              int cw, int lane) {
   using namespace fast;
   const uint32_t pitch = kX * 2;
-  const int nst = (jb.ke - jb.ks + 1) / 2;
   const unsigned char* smem = r.base;
+  JobS* js = r.jobs() + cw;
+  if (lane == 0) {
+    js->zmip = jb.zmip;
+    js->ymip = jb.ymip;
+    js->nx = jb.nx;
+    js->nz = jb.nz;
+    js->j0 = jb.j0;
+    js->xbase = jb.xbase;
+    js->k0g = jb.ks - 2 * g;
+    js->gend = g + (jb.ke - jb.ks + 1) / 2;
+  }
+  __syncwarp();
   float zmax[kJT][kVec];
 #pragma unroll
   for (int j = 0; j < kJT; ++j)
@@ -385,23 +426,23 @@ __device__ __forceinline__ bool fast_consume(const FastJob& jb, const FastRing& 
   bool ok = true;
 
 #pragma unroll 1
-  for (int it = 0; it < nst; ++it, ++g) {
+  for (; g < lds_volatile_s32(&js->gend); ++g) {
     const int s = g % S;
     const unsigned ph = (g / S) & 1;
-    if (!mbar_wait(&r.full[s], ph, err)) {
+    if (!mbar_wait(&r.full()[s], ph, err)) {
       ok = false;
       break;
     }
     const uint32_t lane0 = (uint32_t)(s * stage_slab_bytes(r.Pl)) + lane * (kVec * 2);
     const uint32_t lane1 = lane0 + (uint32_t)slab_row_bytes(r.Pl);
-    const FastRec r0 = r.tab[s * 2 + 0].rec[cw];
-    const FastRec r1 = r.tab[s * 2 + 1].rec[cw];
+    const FastRec r0 = r.tab()[s * 2 + 0].rec[cw];
+    const FastRec r1 = r.tab()[s * 2 + 1].rec[cw];
     // warp-uniform step masks (bit j: step before column j)
     const unsigned adv0 = __ballot_sync(0xffffffffu, lane < kJT && ((r0.adv >> lane) & 1u));
     const unsigned adv1 = __ballot_sync(0xffffffffu, lane < kJT && ((r1.adv >> lane) & 1u));
     StreamPF st0, st1;
-    stream_reset_u16(st0, smem, lane0, pitch, r0.ofirst, jb.P);
-    stream_reset_u16(st1, smem, lane1, pitch, r1.ofirst, jb.P);
+    stream_reset_u16(st0, smem, lane0, pitch, r0.ofirst);
+    stream_reset_u16(st1, smem, lane1, pitch, r1.ofirst);
     const uint32_t w0off = (uint32_t)(off_tab(r.Pl) + (s * 2 + 0) * sizeof(FastRow)) + cw * kJT * 8;
     const uint32_t w1off = w0off + (uint32_t)sizeof(FastRow);
 
@@ -412,8 +453,8 @@ __device__ __forceinline__ bool fast_consume(const FastJob& jb, const FastRing& 
 #pragma unroll
     for (int j = 0; j < kJT; ++j) {
       if (j > 0) {
-        if (adv0 & (1u << j)) stream_step_u16(st0, smem, lane0, pitch, jb.P);
-        if (adv1 & (1u << j)) stream_step_u16(st1, smem, lane1, pitch, jb.P);
+        if (adv0 & (1u << j)) stream_step_u16(st0, smem, pitch);
+        if (adv1 & (1u << j)) stream_step_u16(st1, smem, pitch);
       }
       const f2 w0 = *reinterpret_cast<const f2*>(smem + w0off + j * 8);
       const f2 w1 = *reinterpret_cast<const f2*>(smem + w1off + j * 8);
@@ -440,8 +481,8 @@ __device__ __forceinline__ bool fast_consume(const FastJob& jb, const FastRing& 
     }
     // y-max: combine the four warps in shared memory, then each warp folds
     // 32 columns of both rows into the global y-MIP
-    float* yb0 = r.ybuf + (s * 2 + 0) * kX;
-    float* yb1 = r.ybuf + (s * 2 + 1) * kX;
+    float* yb0 = r.ybuf() + (s * 2 + 0) * kX;
+    float* yb1 = r.ybuf() + (s * 2 + 1) * kX;
 #pragma unroll
     for (int c = 0; c < kVec; ++c) {
       const int yi = yidx(lane * kVec + c);
@@ -449,8 +490,8 @@ __device__ __forceinline__ bool fast_consume(const FastJob& jb, const FastRing& 
       atomicMax(reinterpret_cast<int*>(yb1 + yi), __float_as_int(ym1[c]));
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&r.cdone[s]);
-    if (!mbar_wait(&r.cdone[s], ph, err)) {
+    if (lane == 0) mbar_arrive(&r.cdone()[s]);
+    if (!mbar_wait(&r.cdone()[s], ph, err)) {
       ok = false;
       break;
     }
@@ -460,26 +501,31 @@ __device__ __forceinline__ bool fast_consume(const FastJob& jb, const FastRing& 
       const float y0 = yb0[yi], y1 = yb1[yi];
       yb0[yi] = 0.0f;
       yb1[yi] = 0.0f;
-      const int k0 = jb.ks + 2 * it;
-      if (jb.ymip && jb.xbase + xl < jb.nx) {
-        atomicMax(reinterpret_cast<int*>(jb.ymip + (size_t)k0 * jb.nx + jb.xbase + xl), __float_as_int(y0));
-        if (k0 + 1 < jb.nz)
-          atomicMax(reinterpret_cast<int*>(jb.ymip + (size_t)(k0 + 1) * jb.nx + jb.xbase + xl),
-                    __float_as_int(y1));
+      float* ymip = lds_volatile_ptr(&js->ymip);
+      const int nx = lds_volatile_s32(&js->nx);
+      const int x = lds_volatile_s32(&js->xbase) + xl;
+      const int k0 = lds_volatile_s32(&js->k0g) + 2 * g;
+      if (ymip && x < nx) {
+        atomicMax(reinterpret_cast<int*>(ymip + (size_t)k0 * nx + x), __float_as_int(y0));
+        if (k0 + 1 < lds_volatile_s32(&js->nz))
+          atomicMax(reinterpret_cast<int*>(ymip + (size_t)(k0 + 1) * nx + x), __float_as_int(y1));
       }
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&r.ydone[s]);
+    if (lane == 0) mbar_arrive(&r.ydone()[s]);
   }
 
-  if (jb.zmip) {
-    const int x = jb.xbase + lane * kVec;
+  float* zmip = lds_volatile_ptr(&js->zmip);
+  if (zmip) {
+    const int nx = lds_volatile_s32(&js->nx);
+    const int x = lds_volatile_s32(&js->xbase) + lane * kVec;
+    const int jrow = lds_volatile_s32(&js->j0) + cw * kJT;
 #pragma unroll
     for (int j = 0; j < kJT; ++j) {
-      float* row = jb.zmip + (size_t)(jb.j0 + cw * kJT + j) * jb.nx;
+      float* row = zmip + (size_t)(jrow + j) * nx;
 #pragma unroll
       for (int c = 0; c < kVec; ++c)
-        if (x + c < jb.nx) atomicMax(reinterpret_cast<int*>(row + x + c), __float_as_int(zmax[j][c]));
+        if (x + c < nx) atomicMax(reinterpret_cast<int*>(row + x + c), __float_as_int(zmax[j][c]));
     }
   }
   return ok;

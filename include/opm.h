@@ -162,9 +162,10 @@ typedef struct {
 
 /*
  * opm_batch_create - work lists for up to max_items items and max_units
- * work units (a unit is one 32-column j-tile x 128-column x-tile x row chunk
- * of one item).  Allocates device memory and pinned host memory once; the
- * other batch calls allocate nothing.
+ * (<= 2^26) work units (a unit is one 32-column j-tile x 128-column x-tile x
+ * row chunk of one item; 32 bytes of work list each).  Allocates device
+ * memory and pinned host memory once; the other batch calls allocate nothing
+ * except the CUDA graph of opm_batch_launch_graph.
  * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_OUT_OF_MEMORY, OPM_ERR_CUDA.
  */
 opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out);
@@ -182,23 +183,38 @@ opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out);
  */
 opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk);
 
-/* opm_batch_upload - asynchronous copy of the prepared work list to the
- * device on cuda_stream.  Errors: OPM_ERR_INVALID_ARG, OPM_ERR_CUDA. */
+/* opm_batch_upload - asynchronous copy of the prepared work list (only its
+ * used bytes: a 256-byte header, 192 bytes per item, 32 per output and 32 per
+ * unit) to the device on cuda_stream.
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_CUDA. */
 opm_status opm_batch_upload(opm_batch* b, void* cuda_stream);
 
 /*
  * opm_batch_launch - zeroes the items' outputs and runs the persistent fused
  * projection over all units on cuda_stream (ctas_per_sm in 1..4, 0: 4).
- * Uses only the device copy of the work list, so the two launches can be
- * captured once in a CUDA graph and replayed after later upload calls with
- * the same item count, unit count and slab depth.
- * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_CUDA.
+ * The kernels take the unit and output counts from the device copy of the
+ * work list, so the two launches may be captured in a CUDA graph by the
+ * caller and replayed after later set + upload calls of any content with
+ * the same slab depth (plans of the same theta, step and pixel) and grid.
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED, OPM_ERR_CUDA.
  */
 opm_status opm_batch_launch(opm_batch* b, int ctas_per_sm, void* cuda_stream);
 
-/* Units, items and shared-memory bytes of the prepared batch (any pointer
- * may be NULL).  Errors: OPM_ERR_INVALID_ARG. */
-opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes);
+/*
+ * opm_batch_launch_graph - as opm_batch_launch, through a CUDA graph the
+ * batch owns: captured on first use (on a private stream, so cuda_stream may
+ * be the legacy default stream), re-captured only when the slab depth or the
+ * grid changes, and launched on cuda_stream.  The graph always runs
+ * ctas_per_sm x SM persistent CTAs; those without units return at once.
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED, OPM_ERR_CUDA.
+ */
+opm_status opm_batch_launch_graph(opm_batch* b, int ctas_per_sm, void* cuda_stream);
+
+/* Items, units and shared-memory bytes of the prepared batch, and how many
+ * times opm_batch_launch_graph has captured its graph (any pointer may be
+ * NULL).  Errors: OPM_ERR_INVALID_ARG. */
+opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes,
+                          int* graph_captures);
 
 /* Synchronising diagnostic, as opm_plan_check for the batch's launches. */
 opm_status opm_batch_check(const opm_batch* b);

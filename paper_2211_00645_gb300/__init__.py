@@ -55,8 +55,9 @@ _SIGS = {
     "opm_batch_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "opm_batch_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "opm_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "opm_batch_launch_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "opm_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
-                                      ctypes.POINTER(ctypes.c_int)]),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "opm_batch_check": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_batch_project_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -327,16 +328,25 @@ class Batch:
     def launch(self, ctas_per_sm: int = 0, stream=None):
         _check(load().opm_batch_launch(self._h, int(ctas_per_sm), _stream(stream)), "opm_batch_launch")
 
-    def run(self, ctas_per_sm: int = 0, stream=None):
+    def launch_graph(self, ctas_per_sm: int = 0, stream=None):
+        """``opm_batch_launch_graph``: the launch through the batch's CUDA graph."""
+        _check(load().opm_batch_launch_graph(self._h, int(ctas_per_sm), _stream(stream)), "opm_batch_launch_graph")
+
+    def run(self, ctas_per_sm: int = 0, stream=None, graph: bool = False):
         self.upload(stream)
-        self.launch(ctas_per_sm, stream)
+        if graph:
+            self.launch_graph(ctas_per_sm, stream)
+        else:
+            self.launch(ctas_per_sm, stream)
 
     def info(self):
         n = ctypes.c_int()
         u = ctypes.c_int64()
         sm = ctypes.c_int()
-        _check(load().opm_batch_info(self._h, ctypes.byref(n), ctypes.byref(u), ctypes.byref(sm)), "opm_batch_info")
-        return {"items": n.value, "units": u.value, "smem_bytes": sm.value}
+        gc = ctypes.c_int()
+        _check(load().opm_batch_info(self._h, ctypes.byref(n), ctypes.byref(u), ctypes.byref(sm), ctypes.byref(gc)),
+               "opm_batch_info")
+        return {"items": n.value, "units": u.value, "smem_bytes": sm.value, "graph_captures": gc.value}
 
     def check(self):
         _check(load().opm_batch_check(self._h), "opm_batch_check")

@@ -9,6 +9,15 @@
 // and consumer loops unit after unit on one mbarrier ring whose stage counter
 // carries on across units, so the next unit's slabs stream in while the
 // current one drains.
+//
+// Work-list image (host staging and device copy share it):
+//   [0, 256)            BatchHdr: unit and output-segment counts and offsets
+//   [256, ...)          BatchItemDev per item (TMA descriptor + outputs)
+//   off_segs            BatchSeg per output to zero (z-MIP, y-MIP)
+//   off_units           BatchUnit per work unit, longest first
+// Only the used prefix is copied per upload.  The kernels read the counts
+// from the header, so a launch captured in a CUDA graph stays valid for any
+// later content with the same slab depth.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -16,13 +25,22 @@
 #include <cstring>
 #include <mutex>
 #include <new>
-#include <vector>
+#include <string>
 
 #include "opm_tma.cuh"
 
 namespace opm {
 
 namespace {
+
+struct BatchHdr {
+  int n_units;
+  int n_segs;
+  unsigned off_units;
+  unsigned off_segs;
+};
+
+constexpr size_t kOffItems = 256;
 
 struct BatchItemDev {  // 64-byte aligned through its tensor map
   CUtensorMap tmap;      // raw stack of the item, box {128, 1, P}
@@ -43,8 +61,18 @@ struct __align__(16) BatchSeg {
   long long n;
 };
 
-__global__ void k_batch_zero(const BatchSeg* __restrict__ segs, int nseg) {
-  for (int sgi = blockIdx.y; sgi < nseg; sgi += gridDim.y) {
+constexpr size_t cal256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Bytes of a work-list image with room for max_items items and max_units units.
+constexpr size_t worklist_bytes(size_t max_items, size_t max_units) {
+  return kOffItems + cal256(sizeof(BatchItemDev) * max_items) + cal256(sizeof(BatchSeg) * 2 * max_items) +
+         sizeof(BatchUnit) * max_units;
+}
+
+__global__ void k_batch_zero(const unsigned char* __restrict__ wl) {
+  const BatchHdr hdr = *reinterpret_cast<const BatchHdr*>(wl);
+  const BatchSeg* segs = reinterpret_cast<const BatchSeg*>(wl + hdr.off_segs);
+  for (int sgi = blockIdx.y; sgi < hdr.n_segs; sgi += gridDim.y) {
     const BatchSeg sg = segs[sgi];
     const long long n4 = ((uintptr_t)sg.ptr % 16 == 0) ? sg.n / 4 : 0;
     float4* p4 = reinterpret_cast<float4*>(sg.ptr);
@@ -57,9 +85,11 @@ __global__ void k_batch_zero(const BatchSeg* __restrict__ segs, int nseg) {
 }
 
 __global__ void __launch_bounds__(kThreads, 4)
-k_batch_fast(const BatchItemDev* __restrict__ items, const BatchUnit* __restrict__ units, int nunits, int Pl,
-             unsigned* err) {
+k_batch_fast(const unsigned char* __restrict__ wl, int Pl, unsigned* err) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const BatchHdr hdr = *reinterpret_cast<const BatchHdr*>(wl);
+  const BatchItemDev* items = reinterpret_cast<const BatchItemDev*>(wl + kOffItems);
+  const BatchUnit* units = reinterpret_cast<const BatchUnit*>(wl + hdr.off_units);
   const FastRing ring = fast_ring(smem, Pl);
   fast_ring_init(ring);
   const int warp = threadIdx.x >> 5;
@@ -67,7 +97,7 @@ k_batch_fast(const BatchItemDev* __restrict__ items, const BatchUnit* __restrict
   int g = 0;
   bool ok = true;
 #pragma unroll 1
-  for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+  for (int u = blockIdx.x; u < hdr.n_units && ok; u += gridDim.x) {
     const BatchUnit un = units[u];
     const BatchItemDev* it = items + un.item;
     FastJob jb;
@@ -112,102 +142,47 @@ PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
   return fn;
 }
 
-size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
+bool unit_before(const BatchUnit& a, const BatchUnit& c) {
+  // longest first; ties in generation order (item, j-tile, chunk, x-tile),
+  // which makes the order a pure function of the items without a stable sort
+  const int la = a.ke - a.ks, lc = c.ke - c.ks;
+  if (la != lc) return la > lc;
+  if (a.item != c.item) return a.item < c.item;
+  if (a.jt != c.jt) return a.jt < c.jt;
+  if (a.ks != c.ks) return a.ks < c.ks;
+  return a.xt < c.xt;
+}
 
-}  // namespace
-
-}  // namespace opm
-
-using namespace opm;
-
-struct opm_batch {
-  int max_items;
-  int64_t max_units;
-  int device;
-  int nsm;
-  int smem_optin;
-  size_t off_units, off_segs, off_err, bytes;  // layout shared by host staging and device copy
-  unsigned char* dev;   // device work list
-  unsigned char* host;  // pinned staging
-  cudaEvent_t uploaded; // last upload of the staging has completed
-  bool pending;         // an upload was recorded since the last wait
-  int n_items, n_segs, Pl;
-  int64_t n_units;
-  int attr_set;
+struct WorkList {
+  size_t used;  // bytes of the image to copy
+  int n_items, n_units, n_segs, Pl;
 };
 
-extern "C" {
-
-opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out) {
-  if (!out) return fail(OPM_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (max_items < 1 || max_units < 1 || max_units > (int64_t)1 << 31)
-    return fail(OPM_ERR_INVALID_ARG, "need max_items >= 1 and 1 <= max_units <= 2^31");
-  opm_batch* b = new (std::nothrow) opm_batch();
-  if (!b) return fail(OPM_ERR_OUT_OF_MEMORY, "host allocation of the batch failed");
-  b->max_items = max_items;
-  b->max_units = max_units;
-  b->off_units = al(sizeof(BatchItemDev) * (size_t)max_items, 256);
-  b->off_segs = b->off_units + al(sizeof(BatchUnit) * (size_t)max_units, 256);
-  b->off_err = b->off_segs + al(sizeof(BatchSeg) * 2 * (size_t)max_items, 256);
-  b->bytes = b->off_err + 256;
-  cudaError_t e = cudaGetDevice(&b->device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
-  if (e == cudaSuccess)
-    e = cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->dev), b->bytes);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->host), b->bytes, cudaHostAllocDefault);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMemset(b->dev + b->off_err, 0, 256);
-  if (e != cudaSuccess) {
-    opm_status st = cuda_fail(e, "opm_batch_create");
-    if (b->dev) cudaFree(b->dev);
-    if (b->host) cudaFreeHost(b->host);
-    delete b;
-    return st;
-  }
-  std::memset(b->host, 0, b->bytes);
-  *out = b;
-  return OPM_OK;
-}
-
-opm_status opm_batch_destroy(opm_batch* b) {
-  if (!b) return OPM_OK;
-  cudaError_t e = cudaSuccess, e2;
-  if (b->uploaded && (e2 = cudaEventSynchronize(b->uploaded)) != cudaSuccess) e = e2;
-  if (b->dev && (e2 = cudaFree(b->dev)) != cudaSuccess) e = e2;
-  if (b->host && (e2 = cudaFreeHost(b->host)) != cudaSuccess) e = e2;
-  if (b->uploaded) cudaEventDestroy(b->uploaded);
-  delete b;
-  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "opm_batch_destroy");
-}
-
-}  // extern "C"
-
-extern "C" {
-
-opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk) {
-  if (!b || (!items && n_items > 0)) return fail(OPM_ERR_INVALID_ARG, "batch or items is NULL");
-  if (n_items < 0 || n_items > b->max_items)
-    return fail(OPM_ERR_INVALID_ARG, "n_items must lie in [0, max_items]");
+// Builds the work-list image of `items` into `stage` (room for max_items
+// items and max_units units; 64-byte aligned).  Allocates nothing on
+// success.  `limit_what` names the capacity in error messages.
+opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, int device, unsigned char* stage,
+                          int max_items, int64_t max_units, const char* limit_what, WorkList* out) {
+  if (n_items < 0) return fail(OPM_ERR_INVALID_ARG, "n_items must be >= 0");
+  if (n_items > max_items)
+    return fail(OPM_ERR_UNSUPPORTED, std::to_string(n_items) + " items exceed the " + limit_what + "'s limit of " +
+                                         std::to_string(max_items));
+  if (!items && n_items > 0) return fail(OPM_ERR_INVALID_ARG, "items is NULL");
   if (kchunk < 0) return fail(OPM_ERR_INVALID_ARG, "kchunk must be >= 0");
   if (kchunk == 0) kchunk = 64;
   if (!batch_encode_fn()) return fail(OPM_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is unavailable");
-  // the staging may still be in flight from the previous upload
-  if (b->pending) {
-    cudaError_t e = cudaEventSynchronize(b->uploaded);
-    if (e != cudaSuccess) return cuda_fail(e, "waiting for the previous batch upload");
-    b->pending = false;
-  }
-  BatchItemDev* hitems = reinterpret_cast<BatchItemDev*>(b->host);
-  BatchSeg* hsegs = reinterpret_cast<BatchSeg*>(b->host + b->off_segs);
-  std::vector<BatchUnit> units;
+  const size_t off_segs = cal256(kOffItems + sizeof(BatchItemDev) * (size_t)n_items);
+  const size_t off_units = cal256(off_segs + sizeof(BatchSeg) * 2 * (size_t)n_items);
+  BatchItemDev* hitems = reinterpret_cast<BatchItemDev*>(stage + kOffItems);
+  BatchSeg* hsegs = reinterpret_cast<BatchSeg*>(stage + off_segs);
+  BatchUnit* hunits = reinterpret_cast<BatchUnit*>(stage + off_units);
+  int64_t nunits = 0;
   int Pl = 2, nseg = 0;
   for (int i = 0; i < n_items; ++i) {
     const opm_batch_item& it = items[i];
     const opm_plan* p = it.plan;
     if (!p || !it.raw) return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": NULL plan or raw");
-    if (p->device != b->device)
+    if (p->device != device)
       return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) + ": plan on another device");
     if (!plan_fast_ok(p))
       return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
@@ -250,79 +225,226 @@ opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items,
       for (int c0 = (bd.lo / kchunk) * kchunk; c0 < bd.hi; c0 += kchunk) {
         const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + kchunk);
         if (ks >= ke) continue;
-        for (int xt = 0; xt < xtiles; ++xt) units.push_back(BatchUnit{i, xt, jt, ks, ke, {0, 0, 0}});
+        if (nunits + xtiles > max_units)
+          return fail(OPM_ERR_UNSUPPORTED, std::string("the items need more than the ") + limit_what + "'s limit of " +
+                                               std::to_string(max_units) + " work units (raise kchunk or split)");
+        for (int xt = 0; xt < xtiles; ++xt) hunits[nunits++] = BatchUnit{i, xt, jt, ks, ke, {0, 0, 0}};
       }
     }
   }
-  if ((int64_t)units.size() > b->max_units)
-    return fail(OPM_ERR_UNSUPPORTED, "batch needs " + std::to_string(units.size()) + " units, capacity " +
-                                         std::to_string(b->max_units));
   // longest units first, dealt round-robin to the persistent CTAs
-  std::stable_sort(units.begin(), units.end(),
-                   [](const BatchUnit& a, const BatchUnit& c) { return (a.ke - a.ks) > (c.ke - c.ks); });
-  if (!units.empty()) std::memcpy(b->host + b->off_units, units.data(), sizeof(BatchUnit) * units.size());
-  b->n_items = n_items;
-  b->n_units = (int64_t)units.size();
-  b->n_segs = nseg;
-  b->Pl = Pl;
+  std::sort(hunits, hunits + nunits, unit_before);
+  BatchHdr* hdr = reinterpret_cast<BatchHdr*>(stage);
+  hdr->n_units = (int)nunits;
+  hdr->n_segs = nseg;
+  hdr->off_units = (unsigned)off_units;
+  hdr->off_segs = (unsigned)off_segs;
+  out->used = off_units + sizeof(BatchUnit) * (size_t)nunits;
+  out->n_items = n_items;
+  out->n_units = (int)nunits;
+  out->n_segs = nseg;
+  out->Pl = Pl;
+  return OPM_OK;
+}
+
+// Rows of the zero kernel's grid: its blocks stride over the segments the
+// header lists, so one grid shape serves every content.
+constexpr int kZeroRows = 32;
+
+// Zero kernel, then `grid` persistent CTAs (none when grid == 0), on `s`.
+cudaError_t launch_worklist(const unsigned char* dev_wl, int Pl, int grid, unsigned* err, cudaStream_t s) {
+  k_batch_zero<<<dim3(64, kZeroRows), 256, 0, s>>>(dev_wl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || grid == 0) return e;
+  k_batch_fast<<<grid, kThreads, fast::total(Pl), s>>>(dev_wl, Pl, err);
+  return cudaGetLastError();
+}
+
+cudaError_t set_fast_attrs(int smem_optin) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+}  // namespace
+
+}  // namespace opm
+
+using namespace opm;
+
+struct opm_batch {
+  int max_items;
+  int64_t max_units;
+  int device;
+  int nsm;
+  int smem_optin;
+  size_t bytes;          // work-list capacity; the error word follows at `bytes`
+  unsigned char* dev;    // device work list + error word
+  unsigned char* host;   // pinned staging
+  cudaEvent_t uploaded;  // last upload of the staging has completed
+  bool pending;          // an upload was recorded since the last wait
+  WorkList wl;           // the prepared content
+  int attr_set;
+  cudaStream_t capture;  // private stream the graph is captured on
+  cudaGraphExec_t graph; // zero + persistent kernels for (graph_Pl, graph_grid)
+  int graph_Pl, graph_grid, graph_captures;
+};
+
+extern "C" {
+
+opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out) {
+  if (!out) return fail(OPM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (max_items < 1 || max_units < 1 || max_units > (int64_t)1 << 26)
+    return fail(OPM_ERR_INVALID_ARG, "need max_items >= 1 and 1 <= max_units <= 2^26");
+  opm_batch* b = new (std::nothrow) opm_batch();
+  if (!b) return fail(OPM_ERR_OUT_OF_MEMORY, "host allocation of the batch failed");
+  b->max_items = max_items;
+  b->max_units = max_units;
+  b->bytes = worklist_bytes((size_t)max_items, (size_t)max_units);
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->dev), b->bytes + 256);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->host), b->bytes, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemset(b->dev, 0, kOffItems);           // empty header
+  if (e == cudaSuccess) e = cudaMemset(b->dev + b->bytes, 0, 256);      // error word
+  if (e != cudaSuccess) {
+    opm_status st = cuda_fail(e, "opm_batch_create");
+    if (b->dev) cudaFree(b->dev);
+    if (b->host) cudaFreeHost(b->host);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+    return st;
+  }
+  std::memset(b->host, 0, kOffItems);
+  b->wl = WorkList{kOffItems, 0, 0, 0, 2};
+  *out = b;
+  return OPM_OK;
+}
+
+opm_status opm_batch_destroy(opm_batch* b) {
+  if (!b) return OPM_OK;
+  cudaError_t e = cudaSuccess, e2;
+  if (b->uploaded && (e2 = cudaEventSynchronize(b->uploaded)) != cudaSuccess) e = e2;
+  if (b->graph && (e2 = cudaGraphExecDestroy(b->graph)) != cudaSuccess) e = e2;
+  if (b->capture && (e2 = cudaStreamDestroy(b->capture)) != cudaSuccess) e = e2;
+  if (b->dev && (e2 = cudaFree(b->dev)) != cudaSuccess) e = e2;
+  if (b->host && (e2 = cudaFreeHost(b->host)) != cudaSuccess) e = e2;
+  if (b->uploaded) cudaEventDestroy(b->uploaded);
+  delete b;
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "opm_batch_destroy");
+}
+
+opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk) {
+  if (!b || (!items && n_items > 0)) return fail(OPM_ERR_INVALID_ARG, "batch or items is NULL");
+  if (n_items < 0 || n_items > b->max_items)
+    return fail(OPM_ERR_INVALID_ARG, "n_items must lie in [0, max_items]");
+  // the staging may still be in flight from the previous upload
+  if (b->pending) {
+    cudaError_t e = cudaEventSynchronize(b->uploaded);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the previous batch upload");
+    b->pending = false;
+  }
+  WorkList wl;
+  opm_status st = build_worklist(items, n_items, kchunk, b->device, b->host, b->max_items, b->max_units, "batch", &wl);
+  if (st != OPM_OK) {
+    // leave an empty, valid image behind
+    std::memset(b->host, 0, kOffItems);
+    b->wl = WorkList{kOffItems, 0, 0, 0, 2};
+    return st;
+  }
+  b->wl = wl;
   return OPM_OK;
 }
 
 opm_status opm_batch_upload(opm_batch* b, void* stream) {
   if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(b->dev, b->host, b->off_err, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(b->dev, b->host, b->wl.used, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(b->uploaded, s);
   if (e != cudaSuccess) return cuda_fail(e, "opm_batch_upload");
   b->pending = true;
   return OPM_OK;
 }
 
-opm_status opm_batch_launch(opm_batch* b, int ctas_per_sm, void* stream) {
-  if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
+static opm_status batch_prepare_launch(opm_batch* b, int& ctas_per_sm) {
   if (ctas_per_sm < 0 || ctas_per_sm > 4) return fail(OPM_ERR_INVALID_ARG, "ctas_per_sm must lie in [0, 4]");
   if (ctas_per_sm == 0) ctas_per_sm = 4;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (b->n_segs > 0) {
-    dim3 grid(64, std::min(b->n_segs, 65535));
-    k_batch_zero<<<grid, 256, 0, s>>>(reinterpret_cast<const BatchSeg*>(b->dev + b->off_segs), b->n_segs);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_batch_zero");
-  }
-  if (b->n_units == 0) return OPM_OK;
-  const size_t smem = fast::total(b->Pl);
-  if ((int)smem > b->smem_optin) return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
+  if ((int)fast::total(b->wl.Pl) > b->smem_optin)
+    return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
   if (!b->attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem_optin);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = set_fast_attrs(b->smem_optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_batch_fast)");
     b->attr_set = 1;
   }
-  const int grid = (int)std::min<int64_t>(b->n_units, (int64_t)b->nsm * ctas_per_sm);
-  k_batch_fast<<<grid, kThreads, smem, s>>>(reinterpret_cast<const BatchItemDev*>(b->dev),
-                                            reinterpret_cast<const BatchUnit*>(b->dev + b->off_units),
-                                            (int)b->n_units, b->Pl,
-                                            reinterpret_cast<unsigned*>(b->dev + b->off_err));
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_batch_fast");
+  return OPM_OK;
 }
 
-opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes) {
+opm_status opm_batch_launch(opm_batch* b, int ctas_per_sm, void* stream) {
   if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
-  if (n_items) *n_items = b->n_items;
-  if (n_units) *n_units = b->n_units;
-  if (smem_bytes) *smem_bytes = (int)fast::total(b->Pl);
+  opm_status st = batch_prepare_launch(b, ctas_per_sm);
+  if (st != OPM_OK) return st;
+  const int grid = (int)std::min<int64_t>(b->wl.n_units, (int64_t)b->nsm * ctas_per_sm);
+  cudaError_t e = launch_worklist(b->dev, b->wl.Pl, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
+                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "opm_batch_launch");
+}
+
+opm_status opm_batch_launch_graph(opm_batch* b, int ctas_per_sm, void* stream) {
+  if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
+  opm_status st = batch_prepare_launch(b, ctas_per_sm);
+  if (st != OPM_OK) return st;
+  const int grid = b->nsm * ctas_per_sm;  // every CTA reads the unit count from the device header
+  if (!b->graph || b->graph_Pl != b->wl.Pl || b->graph_grid != grid) {
+    if (b->graph) {
+      cudaError_t e = cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphExecDestroy");
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t le = launch_worklist(b->dev, b->wl.Pl, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
+                                     b->capture);
+    e = cudaStreamEndCapture(b->capture, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return cuda_fail(e, "capturing the batch launch");
+    }
+    b->graph_Pl = b->wl.Pl;
+    b->graph_grid = grid;
+    b->graph_captures += 1;
+  }
+  cudaError_t e = cudaGraphLaunch(b->graph, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes, int* graph_captures) {
+  if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
+  if (n_items) *n_items = b->wl.n_items;
+  if (n_units) *n_units = b->wl.n_units;
+  if (smem_bytes) *smem_bytes = (int)fast::total(b->wl.Pl);
+  if (graph_captures) *graph_captures = b->graph_captures;
   return OPM_OK;
 }
 
 opm_status opm_batch_check(const opm_batch* b) {
   if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
   unsigned word = 0;
+  unsigned char* errp = b->dev + b->bytes;
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMemcpy(&word, b->dev + b->off_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && word) e = cudaMemset(b->dev + b->off_err, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemcpy(&word, errp, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word) e = cudaMemset(errp, 0, sizeof(unsigned));
   if (e != cudaSuccess) return cuda_fail(e, "opm_batch_check");
   if (word) return fail(OPM_ERR_INTERNAL, "device consistency check failed (bits " + std::to_string(word) + ")");
   return OPM_OK;
@@ -345,11 +467,7 @@ namespace {
 constexpr int kStaticItems = 64;
 constexpr int64_t kStaticUnits = 1 << 16;
 constexpr int kStaticDevices = 64;
-constexpr size_t cal256(size_t v) { return (v + 255) / 256 * 256; }
-constexpr size_t kSOffUnits = cal256(sizeof(BatchItemDev) * kStaticItems);
-constexpr size_t kSOffSegs = kSOffUnits + cal256(sizeof(BatchUnit) * kStaticUnits);
-constexpr size_t kSOffErr = kSOffSegs + cal256(sizeof(BatchSeg) * 2 * kStaticItems);
-constexpr size_t kSBytes = kSOffErr + 256;
+constexpr size_t kSBytes = worklist_bytes(kStaticItems, kStaticUnits);  // error word follows
 
 struct StaticDevice {
   bool ready;
@@ -361,21 +479,10 @@ alignas(256) unsigned char g_static_stage[kSBytes];  // host image of the work l
 StaticDevice g_static_dev[kStaticDevices];
 std::mutex g_static_mu;
 
-bool unit_before(const BatchUnit& a, const BatchUnit& c) {
-  // longest first; ties in generation order (item, j-tile, chunk, x-tile),
-  // the order the batch path's stable sort keeps
-  const int la = a.ke - a.ks, lc = c.ke - c.ks;
-  if (la != lc) return la > lc;
-  if (a.item != c.item) return a.item < c.item;
-  if (a.jt != c.jt) return a.jt < c.jt;
-  if (a.ks != c.ks) return a.ks < c.ks;
-  return a.xt < c.xt;
-}
-
 }  // namespace
 }  // namespace opm
 
-static __device__ __align__(256) unsigned char g_static_scratch[opm::kSBytes];
+static __device__ __align__(256) unsigned char g_static_scratch[opm::kSBytes + 256];
 
 namespace opm {
 namespace {
@@ -390,10 +497,7 @@ opm_status static_setup(int dev, StaticDevice** out) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = set_fast_attrs(d.smem_optin);
     if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static set-up");
     if ((uintptr_t)p % 256 != 0) return fail(OPM_ERR_INTERNAL, "static scratch is not 256-byte aligned");
     d.scratch = static_cast<unsigned char*>(p);
@@ -408,115 +512,35 @@ opm_status static_setup(int dev, StaticDevice** out) {
 
 extern "C" opm_status opm_batch_project_static(const opm_batch_item* items, int n_items, int kchunk,
                                                int ctas_per_sm, int check, void* stream) {
-  if (!items && n_items > 0) return fail(OPM_ERR_INVALID_ARG, "items is NULL");
-  if (n_items < 0) return fail(OPM_ERR_INVALID_ARG, "n_items must be >= 0");
-  if (n_items > kStaticItems)
-    return fail(OPM_ERR_UNSUPPORTED, std::to_string(n_items) + " items exceed the static limit of " +
-                                         std::to_string(kStaticItems));
-  if (kchunk < 0) return fail(OPM_ERR_INVALID_ARG, "kchunk must be >= 0");
   if (ctas_per_sm < 0 || ctas_per_sm > 4) return fail(OPM_ERR_INVALID_ARG, "ctas_per_sm must lie in [0, 4]");
-  if (kchunk == 0) kchunk = 64;
   if (ctas_per_sm == 0) ctas_per_sm = 4;
-  if (!batch_encode_fn()) return fail(OPM_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is unavailable");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   StaticDevice* sd = nullptr;
   opm_status st = static_setup(dev, &sd);
   if (st != OPM_OK) return st;
-
-  BatchItemDev* hitems = reinterpret_cast<BatchItemDev*>(g_static_stage);
-  BatchUnit* hunits = reinterpret_cast<BatchUnit*>(g_static_stage + kSOffUnits);
-  BatchSeg* hsegs = reinterpret_cast<BatchSeg*>(g_static_stage + kSOffSegs);
-  int64_t nunits = 0;
-  int Pl = 2, nseg = 0;
-  for (int i = 0; i < n_items; ++i) {
-    const opm_batch_item& it = items[i];
-    const opm_plan* p = it.plan;
-    if (!p || !it.raw) return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": NULL plan or raw");
-    if (p->device != dev) return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) + ": plan on another device");
-    if (!plan_fast_ok(p))
-      return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
-                                           ": plan not eligible (needs pixel <= step and ny >= 32)");
-    const int64_t rp = it.row_pitch ? it.row_pitch : p->ncols;
-    const int64_t pp = it.plane_pitch ? it.plane_pitch : p->nrows * rp;
-    if (rp < p->ncols || pp < p->nrows * rp)
-      return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": pitches smaller than the ROI");
-    if ((uintptr_t)it.raw % 16 != 0 || rp % 8 != 0 || pp % 8 != 0)
-      return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
-                                           ": raw must be 16-byte aligned and pitches multiples of 8 elements");
-    BatchItemDev& d = hitems[i];
-    std::memset(&d, 0, sizeof(d));
-    const cuuint64_t dims[3] = {(cuuint64_t)p->ncols, (cuuint64_t)p->nrows, (cuuint64_t)p->nscan};
-    const cuuint64_t strides[2] = {(cuuint64_t)rp * 2, (cuuint64_t)pp * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kX, 1u, (cuuint32_t)p->P};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult cr = batch_encode_fn()(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t*>(it.raw), dims,
-                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS)
-      return fail(OPM_ERR_CUDA, "item " + std::to_string(i) + ": cuTensorMapEncodeTiled failed (" +
-                                    std::to_string((int)cr) + ")");
-    d.frow = p->view.frow;
-    d.fnlo = p->view.fnlo;
-    d.zmip = it.zmip;
-    d.ymip = it.ymip;
-    d.nz = (int)p->nz;
-    d.ny = (int)p->ny;
-    d.nx = (int)p->nx;
-    d.P = p->P;
-    Pl = std::max(Pl, p->P);
-    if (it.zmip) hsegs[nseg++] = BatchSeg{it.zmip, (long long)(p->ny * p->nx)};
-    if (it.ymip) hsegs[nseg++] = BatchSeg{it.ymip, (long long)(p->nz * p->nx)};
-    if (!it.zmip && !it.ymip) continue;
-    const int xtiles = (int)((p->nx + kX - 1) / kX);
-    const int jtiles = (int)((p->ny + kTileJ - 1) / kTileJ);
-    for (int jt = 0; jt < jtiles; ++jt) {
-      const Band bd = p->hBand[jt];
-      for (int c0 = (bd.lo / kchunk) * kchunk; c0 < bd.hi; c0 += kchunk) {
-        const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + kchunk);
-        if (ks >= ke) continue;
-        if (nunits + xtiles > kStaticUnits)
-          return fail(OPM_ERR_UNSUPPORTED, "the items need more than the static limit of " +
-                                               std::to_string(kStaticUnits) + " work units (raise kchunk or split)");
-        for (int xt = 0; xt < xtiles; ++xt) hunits[nunits++] = BatchUnit{i, xt, jt, ks, ke, {0, 0, 0}};
-      }
-    }
-  }
-  std::sort(hunits, hunits + nunits, unit_before);
-
-  // Pageable host -> device copies: each returns once its source has been
+  WorkList wl;
+  st = build_worklist(items, n_items, kchunk, dev, g_static_stage, kStaticItems, kStaticUnits, "static work list",
+                      &wl);
+  if (st != OPM_OK) return st;
+  if ((int)fast::total(wl.Pl) > sd->smem_optin)
+    return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
+  // Pageable host -> device copy: it returns once its source has been
   // staged, so the host image may be rebuilt by the next call.
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* dv = sd->scratch;
-  if (n_items > 0) e = cudaMemcpyAsync(dv, g_static_stage, sizeof(BatchItemDev) * n_items, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && nunits > 0)
-    e = cudaMemcpyAsync(dv + kSOffUnits, g_static_stage + kSOffUnits, sizeof(BatchUnit) * nunits,
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && nseg > 0)
-    e = cudaMemcpyAsync(dv + kSOffSegs, g_static_stage + kSOffSegs, sizeof(BatchSeg) * nseg, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(dv + kSOffErr, 0, sizeof(unsigned), s);  // error word starts at 0
+  unsigned* err = reinterpret_cast<unsigned*>(dv + kSBytes);
+  e = cudaMemcpyAsync(dv, g_static_stage, wl.used, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);  // error word starts at 0
   if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static upload");
-  if (nseg > 0) {
-    dim3 grid(64, std::min(nseg, 65535));
-    k_batch_zero<<<grid, 256, 0, s>>>(reinterpret_cast<const BatchSeg*>(dv + kSOffSegs), nseg);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_batch_zero");
-  }
-  if (nunits > 0) {
-    const size_t smem = fast::total(Pl);
-    if ((int)smem > sd->smem_optin) return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
-    const int grid = (int)std::min<int64_t>(nunits, (int64_t)sd->nsm * ctas_per_sm);
-    k_batch_fast<<<grid, kThreads, smem, s>>>(reinterpret_cast<const BatchItemDev*>(dv),
-                                              reinterpret_cast<const BatchUnit*>(dv + kSOffUnits), (int)nunits, Pl,
-                                              reinterpret_cast<unsigned*>(dv + kSOffErr));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "launch k_batch_fast");
-  }
+  const int grid = (int)std::min<int64_t>(wl.n_units, (int64_t)sd->nsm * ctas_per_sm);
+  e = launch_worklist(dv, wl.Pl, grid, err, s);
+  if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static launch");
   if (check) {
     unsigned word = 0;
     e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaMemcpy(&word, dv + kSOffErr, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&word, err, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static check");
     if (word) return fail(OPM_ERR_INTERNAL, "device consistency check failed (bits " + std::to_string(word) + ")");
   }

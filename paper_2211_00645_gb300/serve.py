@@ -201,11 +201,23 @@ class Request:
     results: Optional[list] = None   # per channel {"zmip", "ymip"} host tensors
     ring: Optional[PinnedRing] = None  # ring holding ``host``, released once copied
     ring_off: int = -1
+    t_admit: float = 0.0     # copy to the device issued
+    t_launch: float = 0.0    # projection launched
+    res_arena: Optional["DeviceArena"] = None  # pinned arena holding ``results``
+    res_off: int = -1
 
     def release_host(self) -> None:
         if self.ring is not None:
             ring, self.ring = self.ring, None
             ring.release(self.ring_off)
+
+    def release_results(self) -> None:
+        """Returns the pinned result buffers to the server (the views in
+        ``results`` must not be used afterwards)."""
+        if self.res_arena is not None:
+            arena, self.res_arena = self.res_arena, None
+            arena.free(self.res_off)
+            self.results = None
 
     @property
     def shape(self):
@@ -221,6 +233,26 @@ def request_bytes(plan, channels: int) -> int:
     raw = 2 * plan.nscan * plan.nrows * plan.ncols * channels
     outs = 4 * (plan.ny * plan.nx + plan.nz * plan.nx) * channels
     return raw + outs + (1 + 2 * channels) * 256  # one 256-byte alignment gap per sub-buffer
+
+
+def result_bytes(plan, channels: int) -> int:
+    """Pinned host bytes of one request's views: z-MIP and y-MIP per channel."""
+    per = ((4 * plan.ny * plan.nx + 255) // 256 + (4 * plan.nz * plan.nx + 255) // 256) * 256
+    return per * channels
+
+
+def result_views(arena: "DeviceArena", off: int, plan, channels: int, torch):
+    """Per-channel {"zmip", "ymip"} float32 views of a pinned arena range."""
+    out, pos = [], off
+    for _ in range(channels):
+        nz = 4 * plan.ny * plan.nx
+        z = arena.view(pos, nz).view(torch.float32).view(plan.ny, plan.nx)
+        pos += (nz + 255) // 256 * 256
+        ny = 4 * plan.nz * plan.nx
+        y = arena.view(pos, ny).view(torch.float32).view(plan.nz, plan.nx)
+        pos += (ny + 255) // 256 * 256
+        out.append({"zmip": z, "ymip": y})
+    return out
 
 
 def percentile(xs, q):
@@ -270,13 +302,17 @@ class LiveViewServer:
     """Continuous-batching live-view server on one GPU (see module docstring)."""
 
     def __init__(self, plans: PlanCache, budget_bytes: int, max_items: int = 256, max_units: int = 1 << 22,
-                 kchunk: int = 0, ctas_per_sm: int = 0, max_inflight: int = 2, keep_results: bool = True):
+                 kchunk: int = 0, ctas_per_sm: int = 0, max_inflight: int = 2, keep_results: bool = True,
+                 result_bytes: int = 1 << 30):
         import torch
 
         from . import Batch
         self.torch = torch
         self.plans = plans
         self.arena = DeviceArena(budget_bytes, base=torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda"))
+        # pinned destination of the read-back, allocated once
+        self.results = DeviceArena(result_bytes, base=torch.empty(int(result_bytes), dtype=torch.uint8,
+                                                                   pin_memory=True))
         self.h2d = torch.cuda.Stream()
         self.d2h = torch.cuda.Stream()
         self.comp = torch.cuda.Stream()
@@ -311,9 +347,11 @@ class LiveViewServer:
             req = self.waiting[0]
             plan = self.plans.get(req.nscan, req.nrows, req.ncols)
             need = request_bytes(plan, req.channels)
-            if need > self.arena.budget:       # can never fit: refuse, keep serving others
+            if need > self.arena.budget or result_bytes(plan, req.channels) > self.results.budget:
+                # can never fit: refuse, keep serving others
                 self.waiting.popleft()
-                req.error = f"needs {need} bytes, budget {self.arena.budget}"
+                req.error = (f"needs {need} device bytes (budget {self.arena.budget}) and "
+                             f"{result_bytes(plan, req.channels)} result bytes ({self.results.budget})")
                 req.t_done = time.perf_counter()
                 self.rejected.append(req)
                 req.release_host()
@@ -327,6 +365,7 @@ class LiveViewServer:
                 r.raw.view(torch.int16).copy_(req.host.view(torch.int16), non_blocking=True)
                 r.h2d = torch.cuda.Event()
                 r.h2d.record(self.h2d)
+            req.t_admit = time.perf_counter()
             self.resident.append(r)
             self.peak_in_use = max(self.peak_in_use, self.arena.in_use)
 
@@ -344,6 +383,11 @@ class LiveViewServer:
             if full or nitems + r.req.channels > self.max_items:
                 full = True                      # keep arrival order: later requests wait too
                 continue
+            off = self.results.alloc(result_bytes(r.plan, r.req.channels))
+            if off is None:                      # read-back space is busy: wait for a retire
+                full = True
+                continue
+            r.req.res_arena, r.req.res_off = self.results, off
             ready.append(r)
             nitems += r.req.channels
         if not ready:
@@ -360,20 +404,19 @@ class LiveViewServer:
             self.comp.wait_event(r.h2d)
             r.launched = True
         b.upload(self.comp)
-        b.launch(self.ctas, self.comp)
+        b.launch_graph(self.ctas, self.comp)
         ev_c = torch.cuda.Event()
         ev_c.record(self.comp)
         self.d2h.wait_event(ev_c)
+        t = time.perf_counter()
         with torch.cuda.stream(self.d2h):
             for r in ready:
-                res = []
-                for c in range(r.req.channels):
-                    hz = torch.empty(r.z[c].shape, dtype=torch.float32, pin_memory=True)
-                    hy = torch.empty(r.y[c].shape, dtype=torch.float32, pin_memory=True)
-                    hz.copy_(r.z[c], non_blocking=True)
-                    hy.copy_(r.y[c], non_blocking=True)
-                    res.append({"zmip": hz, "ymip": hy})
+                res = result_views(self.results, r.req.res_off, r.plan, r.req.channels, torch)
+                for c, h in enumerate(res):
+                    h["zmip"].copy_(r.z[c], non_blocking=True)
+                    h["ymip"].copy_(r.y[c], non_blocking=True)
                 r.req.results = res
+                r.req.t_launch = t
             ev_d = torch.cuda.Event()
             ev_d.record(self.d2h)
         self.inflight.append((ready, ev_d))
@@ -394,7 +437,7 @@ class LiveViewServer:
         for r in ready:
             r.req.t_done = t
             if not self.keep_results:
-                r.req.results = None
+                r.req.release_results()
             self.arena.free(r.off)
             self.resident.remove(r)
             self.done.append(r.req)
@@ -426,11 +469,13 @@ class PlainServer:
     """Reference path: one request at a time on one stream, synchronous copy
     in, one stand-alone projection per channel, copy out."""
 
-    def __init__(self, plans: PlanCache, keep_results: bool = True):
+    def __init__(self, plans: PlanCache, keep_results: bool = True, result_bytes: int = 1 << 30):
         import torch
         self.torch = torch
         self.plans = plans
         self.keep_results = keep_results
+        self.results = DeviceArena(result_bytes, base=torch.empty(int(result_bytes), dtype=torch.uint8,
+                                                                  pin_memory=True))
         self._lock = threading.Lock()
         self._arrivals: deque = deque()
         self.done: List[Request] = []
@@ -444,20 +489,32 @@ class PlainServer:
         from . import opm_project
         torch = self.torch
         plan = self.plans.get(req.nscan, req.nrows, req.ncols)
+        off = self.results.alloc(result_bytes(plan, req.channels))
+        if off is None:
+            req.error = "result buffers exhausted (keep_results without release_results)"
+            req.t_done = time.perf_counter()
+            self.rejected.append(req)
+            req.release_host()
+            return
+        req.t_admit = time.perf_counter()
         raw = torch.empty(req.host.shape, dtype=torch.uint16, device="cuda")
         raw.view(torch.int16).copy_(req.host.view(torch.int16))
         req.release_host()
-        res = []
+        req.t_launch = time.perf_counter()
+        res = result_views(self.results, off, plan, req.channels, torch)
+        req.res_arena, req.res_off = self.results, off
         n = req.ncols
         for c in range(req.channels):
             ch = raw[:, :, c * n:(c + 1) * n].contiguous()
             z = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device="cuda")
             y = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device="cuda")
             opm_project(plan, ch, z, None, y, None)
-            res.append({"zmip": z.cpu(), "ymip": y.cpu()})
-        torch.cuda.synchronize()
-        req.results = res if self.keep_results else None
+            res[c]["zmip"].copy_(z)
+            res[c]["ymip"].copy_(y)
+        req.results = res
         req.t_done = time.perf_counter()
+        if not self.keep_results:
+            req.release_results()
         self.done.append(req)
 
     def run(self, n_expected: int, timeout_s: float = 600.0, idle=None) -> None:
@@ -535,11 +592,22 @@ class Camera(threading.Thread):
 
 
 def serve_stats(server, t_first: float) -> dict:
-    lat = [r.latency_ms for r in server.done]
-    t_last = max((r.t_done for r in server.done), default=t_first)
+    """Throughput and latency (arrival -> views in host memory) of the
+    served requests, with the latency split into queueing (arrival -> copy
+    issued), copy-in (-> projection launched) and the rest (-> views back)."""
+    done = server.done
+    lat = [r.latency_ms for r in done]
+    t_last = max((r.t_done for r in done), default=t_first)
     span = max(t_last - t_first, 1e-9)
-    ch = sum(r.channels for r in server.done)
-    return {"served": len(server.done), "rejected": len(server.rejected),
-            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "max_ms": max(lat) if lat else None,
-            "stacks_per_s": len(server.done) / span, "volumes_per_s": ch / span, "span_s": span}
+    ch = sum(r.channels for r in done)
+    parts = {"queue": [(r.t_admit - r.t_arrival) * 1e3 for r in done],
+             "copy_in": [(r.t_launch - r.t_admit) * 1e3 for r in done],
+             "finish": [(r.t_done - r.t_launch) * 1e3 for r in done]}
+    out = {"served": len(done), "rejected": len(server.rejected),
+           "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "max_ms": max(lat) if lat else None,
+           "stacks_per_s": len(done) / span, "volumes_per_s": ch / span, "span_s": span}
+    for k, v in parts.items():
+        out[f"{k}_p50_ms"] = percentile(v, 50)
+        out[f"{k}_p99_ms"] = percentile(v, 99)
+    return out
 

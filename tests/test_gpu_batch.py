@@ -133,3 +133,51 @@ def test_batch_rejects_bad_items(lib):
     with pytest.raises(lib.OpmError) as e:
         b.set([{"plan": plan, "raw": raw, "zmip": z}] * 3)    # more items than max_items
     assert e.value.status == lib.OPM_ERR_INVALID_ARG
+
+
+def test_graph_launch_serves_any_content_of_one_slab_depth(lib):
+    """One captured graph replays for batches of different item and unit
+    counts (the counts are read from the device work list)."""
+    b = lib.Batch(max_items=8)
+    items_a, _ = _mixed(lib)
+    b.set(items_a[:2])
+    b.run(graph=True)
+    torch.cuda.synchronize()
+    b.check()
+    first = b.info()
+    assert first["graph_captures"] == 1
+    got_a = [(it["zmip"].clone(), it["ymip"].clone()) for it in items_a[:2]]
+    items_b, _ = _mixed(lib, seed=3)
+    b.set(items_b)
+    b.upload()
+    b.launch_graph()
+    torch.cuda.synchronize()
+    b.check()
+    second = b.info()
+    assert second["units"] != first["units"]
+    expect = 1 if second["smem_bytes"] == first["smem_bytes"] else 2
+    assert second["graph_captures"] == expect
+    got_b = [(None if it["zmip"] is None else it["zmip"].clone(), it["ymip"].clone()) for it in items_b]
+    for it in items_a[:2] + items_b:
+        for k in ("zmip", "ymip"):
+            if it[k] is not None:
+                it[k].fill_(-5.0)
+    e = lib.Batch(max_items=8)
+    e.set(items_a[:2])
+    e.run()
+    e.set(items_b)
+    e.run()
+    torch.cuda.synchronize()
+    for it, (z, y) in zip(items_a[:2] + items_b, got_a + got_b):
+        if z is not None:
+            assert torch.equal(it["zmip"], z)
+        assert torch.equal(it["ymip"], y)
+
+
+def test_graph_launch_with_an_empty_batch(lib):
+    b = lib.Batch(max_items=2)
+    b.set([])
+    b.run(graph=True)
+    torch.cuda.synchronize()
+    b.check()
+    assert b.info()["units"] == 0

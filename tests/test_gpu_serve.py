@@ -23,7 +23,7 @@ def _check_results(reqs):
     """Re-serves each distinct (ring range, shape) on the plain path: the
     ring's bytes are written once, so they still hold what was served."""
     from paper_2211_00645_gb300.serve import PlainServer, PlanCache, Request
-    plain = PlainServer(PlanCache(*GEOM))
+    plain = PlainServer(PlanCache(*GEOM), result_bytes=64 << 20)
     ref = {}
     for req in reqs:
         key = (req.host.data_ptr(), tuple(req.host.shape), req.channels)
@@ -39,7 +39,7 @@ def _check_results(reqs):
 
 def _run(ring, n, budget, rate=None, **cam):
     from paper_2211_00645_gb300.serve import Camera, LiveViewServer, PlanCache
-    srv = LiveViewServer(PlanCache(*GEOM), budget, max_items=16, max_units=1 << 16)
+    srv = LiveViewServer(PlanCache(*GEOM), budget, max_items=16, max_units=1 << 16, result_bytes=64 << 20)
     camera = Camera(srv, ring, SHAPES, n, rate, seed=3, **cam)
     camera.start()
     srv.run(camera.expected(), timeout_s=120)
@@ -92,7 +92,7 @@ def test_oversize_request_is_rejected_others_served(ring):
     from paper_2211_00645_gb300.serve import LiveViewServer, PlanCache, Request, request_bytes
     pc = PlanCache(*GEOM)
     big = max(request_bytes(pc.get(n, r, c), C) for (n, r, c, C) in SHAPES)
-    srv = LiveViewServer(pc, big + 4096, max_items=16, max_units=1 << 16)
+    srv = LiveViewServer(pc, big + 4096, max_items=16, max_units=1 << 16, result_bytes=64 << 20)
     huge = Request(99, 400, 512, 512, 2, torch.empty((400, 512, 1024), dtype=torch.uint16))
     srv.submit(huge)
     reqs = []
@@ -105,3 +105,20 @@ def test_oversize_request_is_rejected_others_served(ring):
     assert [r.rid for r in srv.rejected] == [99] and "budget" in huge.error
     assert len(srv.done) == len(SHAPES) and ring.in_use() == 0
     _check_results(srv.done)
+
+
+def test_results_released_back_to_the_arena(ring):
+    """Without keep_results the pinned read-back space is reused: a small
+    result arena serves many more requests than it holds at once."""
+    from paper_2211_00645_gb300.serve import Camera, LiveViewServer, PlanCache, result_bytes
+    pc = PlanCache(*GEOM)
+    most = max(result_bytes(pc.get(n, r, c), C) for (n, r, c, C) in SHAPES)
+    srv = LiveViewServer(pc, 256 << 20, max_items=16, max_units=1 << 16, keep_results=False,
+                         result_bytes=2 * most + 4096)
+    cam = Camera(srv, ring, SHAPES, 30, None, seed=4)
+    cam.start()
+    srv.run(cam.expected(), timeout_s=120)
+    cam.join(timeout=30)
+    torch.cuda.synchronize()
+    assert len(srv.done) == 30 and srv.results.in_use == 0
+    assert all(r.results is None for r in srv.done)

@@ -94,7 +94,7 @@ def test_limits_are_enforced(lib):
     items = _items(lib, 400)
     with pytest.raises(lib.OpmError) as e:
         lib.batch_project_static(items * 17)             # 68 items > 64
-    assert e.value.status == lib.OPM_ERR_UNSUPPORTED and "static limit" in str(e.value)
+    assert e.value.status == lib.OPM_ERR_UNSUPPORTED and "limit of 64" in str(e.value)
     big = lib.Plan(400, 1024, 2048, 35.0, 0.3, 0.1)
     raw = torch.zeros(big.raw_shape, dtype=torch.uint16, device="cuda")
     z = torch.empty((big.ny, big.nx), device="cuda")

@@ -189,6 +189,27 @@ def cpu_baseline(R, cfg, cols, budget_s=20.0):
             "sample": f"first {cols} of {cfg.ncols} x-columns (project + deskew, {t:.1f} s)"}
 
 
+def tune_serving(torch, plans, ring):
+    """Launch shape of the batched server, tuned on six stacks of the serving
+    mix (one tick's worth) copied to the device."""
+    from paper_2211_00645_gb300.tune import Tuner
+    items, keep = [], []
+    for (n, r, c, C) in opm_synth.serve_shapes(6, seed=11):
+        plan = plans.get(n, r, c)
+        off = ring.acquire(2 * n * r * c * C)
+        raw = ring.view(off, (n, r, c * C)).view(torch.int16).cuda().view(torch.uint16)
+        ring.release(off)
+        keep.append(raw)
+        for ch in range(C):
+            items.append({"plan": plan, "raw": raw[:, :, ch * c:], "row_pitch": C * c, "plane_pitch": r * C * c,
+                          "zmip": torch.empty((plan.ny, plan.nx), device="cuda"),
+                          "ymip": torch.empty((plan.nz, plan.nx), device="cuda")})
+    e = Tuner().tune(items, reps=3)
+    del items, keep
+    torch.cuda.empty_cache()
+    return e
+
+
 def serve_bench(args, torch):
     """Serving comparison on the batched-serving workload: the live-view
     server against the plain per-stack path, first at Poisson arrivals of
@@ -201,6 +222,7 @@ def serve_bench(args, torch):
         plans.get(n, r, c)
     ring = PinnedRing(args.serve_ring_gb << 30, seed=11)
     budget = args.serve_budget_gb << 30
+    tuned = tune_serving(torch, plans, ring)
     out = {"workload": "serving: ROIs rows {256,512,1024} x cols {512,1024,2048}, planes 50..400, 2 channels, "
                        "theta 35, step 0.3, pixel 0.1; z-MIP + y-MIP per channel",
            "budget_bytes": budget, "ring_bytes": ring.nbytes}
@@ -222,7 +244,9 @@ def serve_bench(args, torch):
         st["ring_stalls"] = ring.stalls
         return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
 
-    makers = {"batched": lambda: LiveViewServer(plans, budget, keep_results=False),
+    out["tuned"] = tuned
+    makers = {"batched": lambda: LiveViewServer(plans, budget, keep_results=False, kchunk=tuned["kchunk"],
+                                                ctas_per_sm=tuned["ctas_per_sm"]),
               "plain": lambda: PlainServer(plans, keep_results=False)}
     for name, make in makers.items():
         one(make, None, 16, seed=1)                                   # warm-up: allocators, plans

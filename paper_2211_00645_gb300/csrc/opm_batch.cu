@@ -14,7 +14,9 @@
 //   [0, 256)            BatchHdr: unit and output-segment counts and offsets
 //   [256, ...)          BatchItemDev per item (TMA descriptor + outputs)
 //   off_segs            BatchSeg per output to zero (z-MIP, y-MIP)
-//   off_units           BatchUnit per work unit, longest first
+//   off_lists           per persistent-CTA list: first unit (n_lists + 1)
+//   off_units           WorkUnit per work unit, list by list (a balanced
+//                       longest-first schedule, computed on the host)
 // Only the used prefix is copied per upload.  The kernels read the counts
 // from the header, so a launch captured in a CUDA graph stays valid for any
 // later content with the same slab depth.
@@ -27,6 +29,7 @@
 #include <new>
 #include <string>
 
+#include "opm_sched.h"
 #include "opm_tma.cuh"
 
 namespace opm {
@@ -38,6 +41,9 @@ struct BatchHdr {
   int n_segs;
   unsigned off_units;
   unsigned off_segs;
+  int n_lists;
+  unsigned off_lists;
+  int pad[2];
 };
 
 constexpr size_t kOffItems = 256;
@@ -51,11 +57,6 @@ struct BatchItemDev {  // 64-byte aligned through its tensor map
   int nz, ny, nx, P;
 };
 
-struct __align__(16) BatchUnit {
-  int item, xt, jt, ks, ke;
-  int pad[3];
-};
-
 struct __align__(16) BatchSeg {
   float* ptr;
   long long n;
@@ -66,7 +67,7 @@ constexpr size_t cal256(size_t v) { return (v + 255) / 256 * 256; }
 // Bytes of a work-list image with room for max_items items and max_units units.
 constexpr size_t worklist_bytes(size_t max_items, size_t max_units) {
   return kOffItems + cal256(sizeof(BatchItemDev) * max_items) + cal256(sizeof(BatchSeg) * 2 * max_items) +
-         sizeof(BatchUnit) * max_units;
+         cal256(sizeof(int) * (kMaxLists + 1)) + sizeof(WorkUnit) * max_units;
 }
 
 __global__ void k_batch_zero(const unsigned char* __restrict__ wl) {
@@ -87,18 +88,31 @@ __global__ void k_batch_zero(const unsigned char* __restrict__ wl) {
 __global__ void __launch_bounds__(kThreads, 4)
 k_batch_fast(const unsigned char* __restrict__ wl, int Pl, unsigned* err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const BatchHdr hdr = *reinterpret_cast<const BatchHdr*>(wl);
-  const BatchItemDev* items = reinterpret_cast<const BatchItemDev*>(wl + kOffItems);
-  const BatchUnit* units = reinterpret_cast<const BatchUnit*>(wl + hdr.off_units);
+  const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(wl);
   const FastRing ring = fast_ring(smem, Pl);
   fast_ring_init(ring);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   int g = 0;
   bool ok = true;
+  // this CTA's lists: l = blockIdx.x, blockIdx.x + gridDim.x, ... (one list
+  // when the grid has a CTA per list), each the unit run [lists[l], lists[l + 1])
+  int l = (int)blockIdx.x - (int)gridDim.x;
+  int u = 0, uend = 0;
 #pragma unroll 1
-  for (int u = blockIdx.x; u < hdr.n_units && ok; u += gridDim.x) {
-    const BatchUnit un = units[u];
+  while (ok) {
+    if (u >= uend) {
+      const int* lists = reinterpret_cast<const int*>(wl + hdr->off_lists);
+      do {
+        l += gridDim.x;
+        if (l >= hdr->n_lists) break;
+        u = lists[l];
+        uend = lists[l + 1];
+      } while (u >= uend);
+      if (u >= uend) break;
+    }
+    const WorkUnit un = reinterpret_cast<const WorkUnit*>(wl + hdr->off_units)[u++];
+    const BatchItemDev* items = reinterpret_cast<const BatchItemDev*>(wl + kOffItems);
     const BatchItemDev* it = items + un.item;
     FastJob jb;
     jb.tmap = &it->tmap;
@@ -142,27 +156,17 @@ PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
   return fn;
 }
 
-bool unit_before(const BatchUnit& a, const BatchUnit& c) {
-  // longest first; ties in generation order (item, j-tile, chunk, x-tile),
-  // which makes the order a pure function of the items without a stable sort
-  const int la = a.ke - a.ks, lc = c.ke - c.ks;
-  if (la != lc) return la > lc;
-  if (a.item != c.item) return a.item < c.item;
-  if (a.jt != c.jt) return a.jt < c.jt;
-  if (a.ks != c.ks) return a.ks < c.ks;
-  return a.xt < c.xt;
-}
-
 struct WorkList {
   size_t used;  // bytes of the image to copy
-  int n_items, n_units, n_segs, Pl;
+  int n_items, n_units, n_segs, n_lists, Pl;
 };
 
 // Builds the work-list image of `items` into `stage` (room for max_items
 // items and max_units units; 64-byte aligned).  Allocates nothing on
 // success.  `limit_what` names the capacity in error messages.
-opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, int device, unsigned char* stage,
-                          int max_items, int64_t max_units, const char* limit_what, WorkList* out) {
+opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, int device, int nlists,
+                          unsigned char* stage, int max_items, int64_t max_units, const char* limit_what,
+                          WorkList* out) {
   if (n_items < 0) return fail(OPM_ERR_INVALID_ARG, "n_items must be >= 0");
   if (n_items > max_items)
     return fail(OPM_ERR_UNSUPPORTED, std::to_string(n_items) + " items exceed the " + limit_what + "'s limit of " +
@@ -172,10 +176,12 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
   if (kchunk == 0) kchunk = 64;
   if (!batch_encode_fn()) return fail(OPM_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is unavailable");
   const size_t off_segs = cal256(kOffItems + sizeof(BatchItemDev) * (size_t)n_items);
-  const size_t off_units = cal256(off_segs + sizeof(BatchSeg) * 2 * (size_t)n_items);
+  const size_t off_lists = cal256(off_segs + sizeof(BatchSeg) * 2 * (size_t)n_items);
+  const size_t off_units = cal256(off_lists + sizeof(int) * (size_t)(nlists + 1));
   BatchItemDev* hitems = reinterpret_cast<BatchItemDev*>(stage + kOffItems);
   BatchSeg* hsegs = reinterpret_cast<BatchSeg*>(stage + off_segs);
-  BatchUnit* hunits = reinterpret_cast<BatchUnit*>(stage + off_units);
+  int* hlists = reinterpret_cast<int*>(stage + off_lists);
+  WorkUnit* hunits = reinterpret_cast<WorkUnit*>(stage + off_units);
   int64_t nunits = 0;
   int Pl = 2, nseg = 0;
   for (int i = 0; i < n_items; ++i) {
@@ -228,21 +234,25 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
         if (nunits + xtiles > max_units)
           return fail(OPM_ERR_UNSUPPORTED, std::string("the items need more than the ") + limit_what + "'s limit of " +
                                                std::to_string(max_units) + " work units (raise kchunk or split)");
-        for (int xt = 0; xt < xtiles; ++xt) hunits[nunits++] = BatchUnit{i, xt, jt, ks, ke, {0, 0, 0}};
+        for (int xt = 0; xt < xtiles; ++xt) hunits[nunits++] = WorkUnit{i, xt, jt, ks, ke, 0, 0, 0};
       }
     }
   }
-  // longest units first, dealt round-robin to the persistent CTAs
-  std::sort(hunits, hunits + nunits, unit_before);
+  // balanced lists of units, one per persistent CTA
+  schedule_lpt(hunits, (int)nunits, nlists, hlists);
   BatchHdr* hdr = reinterpret_cast<BatchHdr*>(stage);
+  std::memset(hdr, 0, sizeof(*hdr));
   hdr->n_units = (int)nunits;
   hdr->n_segs = nseg;
   hdr->off_units = (unsigned)off_units;
   hdr->off_segs = (unsigned)off_segs;
-  out->used = off_units + sizeof(BatchUnit) * (size_t)nunits;
+  hdr->n_lists = nlists;
+  hdr->off_lists = (unsigned)off_lists;
+  out->used = off_units + sizeof(WorkUnit) * (size_t)nunits;
   out->n_items = n_items;
   out->n_units = (int)nunits;
   out->n_segs = nseg;
+  out->n_lists = nlists;
   out->Pl = Pl;
   return OPM_OK;
 }
@@ -324,7 +334,7 @@ opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out) {
     return st;
   }
   std::memset(b->host, 0, kOffItems);
-  b->wl = WorkList{kOffItems, 0, 0, 0, 2};
+  b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2};
   *out = b;
   return OPM_OK;
 }
@@ -353,11 +363,13 @@ opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items,
     b->pending = false;
   }
   WorkList wl;
-  opm_status st = build_worklist(items, n_items, kchunk, b->device, b->host, b->max_items, b->max_units, "batch", &wl);
+  const int nlists = std::min(b->nsm * 4, kMaxLists);
+  opm_status st = build_worklist(items, n_items, kchunk, b->device, nlists, b->host, b->max_items, b->max_units,
+                                 "batch", &wl);
   if (st != OPM_OK) {
     // leave an empty, valid image behind
     std::memset(b->host, 0, kOffItems);
-    b->wl = WorkList{kOffItems, 0, 0, 0, 2};
+    b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2};
     return st;
   }
   b->wl = wl;
@@ -521,8 +533,8 @@ extern "C" opm_status opm_batch_project_static(const opm_batch_item* items, int 
   opm_status st = static_setup(dev, &sd);
   if (st != OPM_OK) return st;
   WorkList wl;
-  st = build_worklist(items, n_items, kchunk, dev, g_static_stage, kStaticItems, kStaticUnits, "static work list",
-                      &wl);
+  st = build_worklist(items, n_items, kchunk, dev, std::min(sd->nsm * 4, kMaxLists), g_static_stage, kStaticItems,
+                      kStaticUnits, "static work list", &wl);
   if (st != OPM_OK) return st;
   if ((int)fast::total(wl.Pl) > sd->smem_optin)
     return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");

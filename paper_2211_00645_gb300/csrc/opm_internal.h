@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "opm.h"
+#include "opm_sched.h"
 
 namespace opm {
 
@@ -71,6 +72,9 @@ struct PlanView {
   unsigned* err;      // error word
   const FastRow* frow;  // [ntile][nz] fast-kernel tables (NULL unless fast_ok)
   const int* fnlo;      // [ntile][nz] first staged plane of each (tile, row)
+  const WorkUnit* units;  // fast-kernel work units, list by list (NULL unless fast_ok)
+  const int* lists;       // [nlists + 1] first unit of each persistent CTA's list
+  int nunits, nlists;
   int nscan, nrows, ncols, nz, ny, nx, J0;
   int linear;         // 1 LINEAR, 0 NEAREST
   float rinv;         // step / pixel (float), used only to size search windows
@@ -90,6 +94,8 @@ struct opm_plan {
   std::vector<float> hYinit;
   std::vector<opm::FastRow> hFrow;  // fast-kernel tables (when fast_ok)
   std::vector<int> hFnlo;
+  std::vector<opm::WorkUnit> hUnits;  // fast-kernel schedule (when fast_ok and a device exists)
+  std::vector<int> hLists;
   int device;        // -1: created without a device
   void* dmem;        // one allocation holding every device table
   opm::PlanView view;

@@ -235,13 +235,43 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
     delete p;
     return cuda_fail(e, "cudaGetDevice");
   }
+  // The fast kernel's work units (x-tile, j-tile, chunk of kChunkRows rows of
+  // the tile's band) on balanced lists, one per persistent CTA.
+  if (p->fast_ok) {
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    try {
+      const int xtiles = (int)((ncols + kUnitX - 1) / kUnitX);
+      for (int jt = 0; jt < (int)p->hBand.size(); ++jt) {
+        const Band bd = p->hBand[jt];
+        for (int c0 = (bd.lo / kChunkRows) * kChunkRows; c0 < bd.hi; c0 += kChunkRows) {
+          const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + kChunkRows);
+          if (ks >= ke) continue;
+          for (int xt = 0; xt < xtiles; ++xt) p->hUnits.push_back(WorkUnit{0, xt, jt, ks, ke, 0, 0, 0});
+        }
+      }
+      if (p->hUnits.size() > (size_t)INT32_MAX) p->fast_ok = 0;
+      const int nlists = std::min(std::max(nsm, 1) * 4, kMaxLists);
+      p->hLists.assign(nlists + 1, 0);
+      schedule_lpt(p->hUnits.data(), (int)p->hUnits.size(), nlists, p->hLists.data());
+    } catch (const std::bad_alloc&) {
+      delete p;
+      return fail(OPM_ERR_OUT_OF_MEMORY, "host allocation of the plan schedule failed");
+    }
+  }
   const size_t szA = align256(sizeof(Split) * p->hA.size());
   const size_t szB = align256(sizeof(Split) * p->hB.size());
   const size_t szT = align256(sizeof(Band) * p->hBand.size());
   const size_t szY = align256(sizeof(float) * p->hYinit.size());
   const size_t szF = align256(sizeof(FastRow) * p->hFrow.size());
   const size_t szN = align256(sizeof(int) * p->hFnlo.size());
-  const size_t total = szA + szB + szT + szY + szF + szN + 256;
+  const size_t szU = align256(sizeof(WorkUnit) * p->hUnits.size());
+  const size_t szL = align256(sizeof(int) * p->hLists.size());
+  const size_t total = szA + szB + szT + szY + szF + szN + szU + szL + 256;
   e = cudaMalloc(&p->dmem, total);
   if (e != cudaSuccess) {
     delete p;
@@ -254,7 +284,9 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
   float* dY = reinterpret_cast<float*>(base + szA + szB + szT);
   FastRow* dF = reinterpret_cast<FastRow*>(base + szA + szB + szT + szY);
   int* dN = reinterpret_cast<int*>(base + szA + szB + szT + szY + szF);
-  unsigned* dE = reinterpret_cast<unsigned*>(base + szA + szB + szT + szY + szF + szN);
+  WorkUnit* dU = reinterpret_cast<WorkUnit*>(base + szA + szB + szT + szY + szF + szN);
+  int* dL = reinterpret_cast<int*>(base + szA + szB + szT + szY + szF + szN + szU);
+  unsigned* dE = reinterpret_cast<unsigned*>(base + szA + szB + szT + szY + szF + szN + szU + szL);
   if ((e = cudaMemcpy(dA, p->hA.data(), sizeof(Split) * p->hA.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(dB, p->hB.data(), sizeof(Split) * p->hB.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(dT, p->hBand.data(), sizeof(Band) * p->hBand.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -263,6 +295,11 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
        (e = cudaMemcpy(dF, p->hFrow.data(), sizeof(FastRow) * p->hFrow.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (!p->hFnlo.empty() &&
        (e = cudaMemcpy(dN, p->hFnlo.data(), sizeof(int) * p->hFnlo.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!p->hUnits.empty() &&
+       (e = cudaMemcpy(dU, p->hUnits.data(), sizeof(WorkUnit) * p->hUnits.size(), cudaMemcpyHostToDevice)) !=
+           cudaSuccess) ||
+      (!p->hLists.empty() &&
+       (e = cudaMemcpy(dL, p->hLists.data(), sizeof(int) * p->hLists.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (e = cudaMemset(dE, 0, 256)) != cudaSuccess) {
     cudaFree(p->dmem);
     delete p;
@@ -277,6 +314,10 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
   v.err = dE;
   v.frow = p->hFrow.empty() ? nullptr : dF;
   v.fnlo = p->hFnlo.empty() ? nullptr : dN;
+  v.units = p->hUnits.empty() ? nullptr : dU;
+  v.lists = p->hLists.empty() ? nullptr : dL;
+  v.nunits = (int)p->hUnits.size();
+  v.nlists = p->hLists.empty() ? 0 : (int)p->hLists.size() - 1;
   v.nscan = (int)nscan;
   v.nrows = (int)nrows;
   v.ncols = (int)ncols;

@@ -30,7 +30,8 @@
 //                  FP32x2 FMAs, one branch per column step, and each tile's
 //                  row band split into 128-row chunks whose z-maxima combine
 //                  by atomic max, which balances tiles of very different band
-//                  length.
+//                  length; a persistent grid of 4 CTAs per SM walks the
+//                  chunks.
 //  k_project_gen   every output (z-sum, first argmax), uint16 or FP32 input,
 //                  any tile (partial last tile, column steps of several
 //                  planes), one row per stage, whole band per CTA.
@@ -54,45 +55,56 @@ struct ProjArgs {
   float* ymip;
   int32_t* argz;
   int P;       // staged planes per row
-  int kchunk;  // rows per work unit (fast kernel)
   int jt0;     // first j-tile of this launch
 };
 
-// Fast kernel: one job per CTA.  Grid (x-tile, j-tile, chunk): the CTAs
-// sharing a camera row's planes run side by side, so their slab rows combine
-// into whole DRAM pages.
+// Fast kernel, persistent: one CTA per list of the plan's balanced schedule
+// (units of 128 rows of one j-tile at one x-tile).  The stage counter
+// carries on across a CTA's units, so the next unit's slabs stream in while
+// the current one drains.
 __global__ void __launch_bounds__(kThreads, 4)
 k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
   const PlanView& v = args.v;
-  const int jt = blockIdx.y;
-  const Band band = v.band[jt];
-  FastJob jb;
-  jb.ks = max(band.lo, (int)blockIdx.z * args.kchunk);
-  jb.ke = min(band.hi, ((int)blockIdx.z + 1) * args.kchunk);
-  if (jb.ks >= jb.ke) return;
-  jb.tmap = &tmap;
-  jb.rows = v.frow + (size_t)jt * v.nz;
-  jb.nlos = v.fnlo + (size_t)jt * v.nz;
-  jb.zmip = args.zmip;
-  jb.ymip = args.ymip;
-  jb.nz = v.nz;
-  jb.nx = v.nx;
-  jb.j0 = tile_j0(jt, v.ny);
-  jb.xbase = blockIdx.x * kX;
-  jb.P = args.P;
-
   extern __shared__ __align__(128) unsigned char smem[];
   const FastRing ring = fast_ring(smem, args.P);
   fast_ring_init(ring);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   int g = 0;
-  if (warp == 0) {
-    const bool ok = fast_produce(jb, ring, g, v.err, lane);
-    fast_drain(ring, g, ok, v.err);
-  } else {
-    fast_consume(jb, ring, g, v.err, warp - 1, lane);
+  bool ok = true;
+  int l = (int)blockIdx.x - (int)gridDim.x;
+  int u = 0, uend = 0;
+#pragma unroll 1
+  while (ok) {
+    if (u >= uend) {
+      do {
+        l += gridDim.x;
+        if (l >= v.nlists) break;
+        u = v.lists[l];
+        uend = v.lists[l + 1];
+      } while (u >= uend);
+      if (u >= uend) break;
+    }
+    const WorkUnit un = v.units[u++];
+    FastJob jb;
+    jb.ks = un.ks;
+    jb.ke = un.ke;
+    jb.tmap = &tmap;
+    jb.rows = v.frow + (size_t)un.jt * v.nz;
+    jb.nlos = v.fnlo + (size_t)un.jt * v.nz;
+    jb.zmip = args.zmip;
+    jb.ymip = args.ymip;
+    jb.nz = v.nz;
+    jb.nx = v.nx;
+    jb.j0 = tile_j0(un.jt, v.ny);
+    jb.xbase = un.xt * kX;
+    jb.P = args.P;
+    if (warp == 0)
+      ok = fast_produce(jb, ring, g, v.err, lane);
+    else
+      ok = fast_consume(jb, ring, g, v.err, warp - 1, lane);
   }
+  if (warp == 0) fast_drain(ring, g, ok, v.err);
 }
 
 // =====================================================================
@@ -473,10 +485,9 @@ opm_status launch_fast(const opm_plan* p, const CUtensorMap& map, const ProjArgs
   opm_status st = prepare_kernel(k_project_fast, p->device, done);
   if (st != OPM_OK) return st;
   const PlanView& v = p->view;
-  const int xtiles = (v.nx + kX - 1) / kX;
-  const int chunks = (v.nz + args.kchunk - 1) / args.kchunk;
-  if (chunks > 65535 || tiles > 65535) return fail(OPM_ERR_UNSUPPORTED, "projection grid exceeds launch limits");
-  dim3 grid(xtiles, tiles, chunks);
+  if (!v.units || !v.lists) return fail(OPM_ERR_INTERNAL, "plan has no fast-kernel schedule");
+  const int grid = std::min(v.nunits, v.nlists);
+  if (grid == 0) return OPM_OK;
   k_project_fast<<<grid, kThreads, fast::total(args.P), s>>>(map, args);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_fast");
@@ -555,7 +566,6 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
   args.ymip = ymip;
   args.argz = argz;
   args.P = P;
-  args.kchunk = kChunkRows;
   args.jt0 = 0;
   CUtensorMap map;
   opm_status st = u16 ? encode_raw<uint16_t>(v, raw, P, &map) : encode_raw<float>(v, raw, P, &map);

@@ -17,12 +17,12 @@ constexpr int kJT = kTileJ / kNW;    // columns j per compute warp (8)
 constexpr int kThreads = 32 * (kNW + 1);
 constexpr int kVec = 4;              // columns x per lane
 constexpr int kX = 32 * kVec;        // columns x per CTA
-constexpr int kChunkRows = 64;       // rows per work unit of the fast kernel
 constexpr int kStagesFast = 6;       // TMA ring depth, fast kernel
 constexpr int kStagesGen = 4;        // TMA ring depth, general kernel
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a launch takes < 10 ms
 
 static_assert(kJT * kNW == kTileJ, "tile");
+static_assert(kX == kUnitX, "work units and the fast kernels' x-tiles agree");
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

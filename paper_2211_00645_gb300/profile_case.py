@@ -5,6 +5,8 @@ paper_2211_00645_gb300.profile_case ...``).
   --kernel project   fused z-MIP + y-MIP live view (uint16 in)
   --kernel deskew    full deskewed FP32 volume
   --kernel batch     batched live view over a mix of serving-sized stacks
+  --kernel batch1    the named stack alone through the persistent batch kernel
+                     (--kchunk, --ctas: its launch shape)
   --nscan N          override the stack's scan-plane count (smaller captures)
 
 Content: the named configuration's Poisson+blob stack for project/deskew
@@ -28,7 +30,9 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["project", "deskew", "batch"], required=True)
+    ap.add_argument("--kernel", choices=["project", "deskew", "batch", "batch1"], required=True)
+    ap.add_argument("--kchunk", type=int, default=0)
+    ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--config", default="liveview_200x512x2048")
     ap.add_argument("--nscan", type=int, default=0)
     ap.add_argument("--launches", type=int, default=3)
@@ -54,12 +58,12 @@ def main(argv=None):
                               "ymip": torch.empty((plan.nz, plan.nx), device="cuda")})
             keep.append(raw)
         b = opm.Batch(max_items=len(items), max_units=1 << 22)
-        b.set(items)
+        b.set(items, args.kchunk)
         b.upload()
-        desc = {"items": len(items), "shapes": shapes, **b.info()}
+        desc = {"items": len(items), "shapes": shapes, "kchunk": args.kchunk, "ctas": args.ctas, **b.info()}
 
         def launch():
-            b.launch(0, s)
+            b.launch(args.ctas, s)
     else:
         cfg = opm_synth.CONFIGS[args.config]
         if args.nscan:
@@ -68,7 +72,17 @@ def main(argv=None):
         plan = opm.Plan(cfg.nscan, cfg.nrows, cfg.ncols, cfg.theta_deg, cfg.step, cfg.pixel)
         raw = torch.from_numpy(R.view(np.int16)).cuda().view(torch.uint16)
         desc = {"config": cfg.name, "raw": list(cfg.shape), "grid": [plan.nz, plan.ny, plan.nx]}
-        if args.kernel == "project":
+        if args.kernel == "batch1":
+            item = {"plan": plan, "raw": raw, "zmip": torch.empty((plan.ny, plan.nx), device="cuda"),
+                    "ymip": torch.empty((plan.nz, plan.nx), device="cuda")}
+            b = opm.Batch(max_items=1, max_units=1 << 22)
+            b.set([item], args.kchunk)
+            b.upload()
+            desc.update({"kchunk": args.kchunk, "ctas": args.ctas, **b.info()})
+
+            def launch():
+                b.launch(args.ctas, s)
+        elif args.kernel == "project":
             zmip = torch.empty((plan.ny, plan.nx), device="cuda")
             ymip = torch.empty((plan.nz, plan.nx), device="cuda")
 

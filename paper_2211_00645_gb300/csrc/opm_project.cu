@@ -28,7 +28,7 @@
 //                  host with the kernel's own arithmetic).  Two rows per stage
 //                  (one 3-input max per voxel pair into the z-max), packed
 //                  FP32x2 FMAs, one branch per column step, and each tile's
-//                  row band split into 128-row chunks whose z-maxima combine
+//                  row band split into 256-row chunks whose z-maxima combine
 //                  by atomic max, which balances tiles of very different band
 //                  length; a persistent grid of 4 CTAs per SM walks the
 //                  chunks.
@@ -59,7 +59,7 @@ struct ProjArgs {
 };
 
 // Fast kernel, persistent: one CTA per list of the plan's balanced schedule
-// (units of 128 rows of one j-tile at one x-tile).  The stage counter
+// (units of 256 rows of one j-tile at one x-tile).  The stage counter
 // carries on across a CTA's units, so the next unit's slabs stream in while
 // the current one drains.
 __global__ void __launch_bounds__(kThreads, 4)

@@ -21,7 +21,7 @@ static_assert(sizeof(WorkUnit) == 32, "WorkUnit is 32 bytes");
 
 // Rows per work unit of the single-stack fast projection, and columns x
 // per unit (one TMA box row of the fast kernels).
-constexpr int kChunkRows = 128;
+constexpr int kChunkRows = 256;
 constexpr int kUnitX = 128;
 
 // Upper bound on the number of CTA lists (4 CTAs per SM on up to 256 SMs).

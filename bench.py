@@ -41,19 +41,21 @@ UNIT = "GB/s"
 # the stored ncu traffic figure.
 KERNEL_SOURCES = {
     "liveview": ["csrc/opm_project.cu", "csrc/opm_tma.cuh", "csrc/opm_common.cuh", "csrc/opm_internal.h",
-                 "../include/opm.h"],
-    "volume_f32": ["csrc/opm_deskew.cu", "csrc/opm_common.cuh", "csrc/opm_internal.h", "../include/opm.h"],
+                 "csrc/opm_sched.h", "csrc/opm_plan.cu", "../include/opm.h"],
+    "volume_f32": ["csrc/opm_deskew.cu", "csrc/opm_common.cuh", "csrc/opm_internal.h", "csrc/opm_sched.h",
+                   "../include/opm.h"],
 }
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per full-size
 # launch from ncu captures, keyed by the hash of the kernel's sources at
 # capture time (reported as null once a source has changed).  liveview:
-# captured at full size (200 x 512 x 2048).  volume_f32: captured with 100
-# scan planes (212.2 MB read, 2963.6 MB written) and scaled to 200 planes,
-# reads by the raw bytes (x2.0) and writes by the volume bytes (x1.416).
+# captured at full size (200 x 512 x 2048): 451.05 MB read + 7.84 MB written.
+# volume_f32: captured with 100 scan planes (212.38 MB read, 2963.47 MB
+# written) and scaled to 200 planes, reads by the raw bytes (x2.0) and writes
+# by the volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "liveview": {"src_sha": "9249fc0e1141", "bytes_per_launch": 457194752},
-    "volume_f32": {"src_sha": "8ca5acccbe79", "bytes_per_launch": 4620994687},
+    "liveview": {"src_sha": "43a3ec7ec6b4", "bytes_per_launch": 458893312},
+    "volume_f32": {"src_sha": "70fa4038faa2", "bytes_per_launch": 4621287526},
 }
 
 
@@ -223,6 +225,20 @@ def serve_bench(args, torch):
     ring = PinnedRing(args.serve_ring_gb << 30, seed=11)
     budget = args.serve_budget_gb << 30
     tuned = tune_serving(torch, plans, ring)
+
+    def link_gbs():
+        """Pinned host -> device copy rate right now (the serving bound)."""
+        n = min(ring.nbytes, 2 << 30)
+        dst = torch.empty(n, dtype=torch.uint8, device="cuda")
+        dst.copy_(ring.buf[:n])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(3):
+            dst.copy_(ring.buf[:n], non_blocking=True)
+        torch.cuda.synchronize()
+        return round(3 * n / (time.perf_counter() - t) / 1e9, 1)
+
+    link0 = link_gbs()
     out = {"workload": "serving: ROIs rows {256,512,1024} x cols {512,1024,2048}, planes 50..400, 2 channels, "
                        "theta 35, step 0.3, pixel 0.1; z-MIP + y-MIP per channel",
            "budget_bytes": budget, "ring_bytes": ring.nbytes}
@@ -245,6 +261,7 @@ def serve_bench(args, torch):
         return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
 
     out["tuned"] = tuned
+    mean_raw = sum(2 * n * r * c * C for (n, r, c, C) in shapes) / len(shapes)
     makers = {"batched": lambda: LiveViewServer(plans, budget, keep_results=False, kchunk=tuned["kchunk"],
                                                 ctas_per_sm=tuned["ctas_per_sm"]),
               "plain": lambda: PlainServer(plans, keep_results=False)}
@@ -254,6 +271,10 @@ def serve_bench(args, torch):
             if n > 0:
                 ring.stalls = 0
                 out.setdefault(phase, {"rate_per_s": rate, "stacks": n})[name] = one(make, rate, n, seed=2)
+    link1 = link_gbs()
+    out["h2d_link_gbs"] = {"before": link0, "after": link1}
+    out["mean_raw_bytes"] = round(mean_raw)
+    out["link_bound_stacks_per_s"] = round(min(link0, link1) * 1e9 / mean_raw, 1)
     return out
 
 
@@ -342,21 +363,42 @@ def main():
     ms_step = pdist.max_over_ranks(total_ms / K, device=dev)
     opm.opm_plan_check(plan)
 
-    # ---- end to end through the C ABI: pinned host raw in, live view out
+    # ---- end to end through the C ABI: every step copies its stack in from
+    # pinned host memory and its live view back out.  Two device stack
+    # buffers: the copy of step i + 1 (copy stream) overlaps the compute of
+    # step i (compute stream).
     E = max(10, K // 10)
+    raws = [raw, torch.empty_like(raw)]
+    copy_s = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+
+    def step_on(r):
+        opm.opm_project(plan, r, zmip, None, ymip, None, stream)
+        opm.opm_deskew(plan, r, vol, stream)
+
     torch.cuda.synchronize()
     pdist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(E):
-        raw.view(torch.int16).copy_(host_raw, non_blocking=True)
-        step()
+    copy_s.wait_event(e0)
+    for i in range(E):
+        b = i % 2
+        if i >= 2:
+            copy_s.wait_event(freed[b])           # step i - 2 is done with this buffer
+        with torch.cuda.stream(copy_s):
+            raws[b].view(torch.int16).copy_(host_raw, non_blocking=True)
+        copied[b].record(copy_s)
+        stream.wait_event(copied[b])
+        step_on(raws[b])
+        freed[b].record(stream)
         host_z.copy_(zmip, non_blocking=True)
         host_y.copy_(ymip, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = pdist.max_over_ranks(e0.elapsed_time(e1) / E, device=dev)
+    del raws
 
     if rank != 0:
         dist.destroy_process_group()

@@ -100,6 +100,18 @@ opm_status opm_deskew(const opm_plan* plan, const void* raw, opm_dtype in_t,
                       void* vol, opm_dtype out_t, void* cuda_stream);
 
 /*
+ * opm_deskew_dual - the deskew of opm_deskew (Fig. 2c) written twice in one pass over
+ * the raw stack: as FP32 into vol_f32 and rounded to nearest (ties to even,
+ * clamped to [0, 65535]) into vol_u16, both [nz][ny][nx] device arrays owned
+ * by the caller.  Each uint16 voxel is the rounding of the FP32 voxel beside
+ * it.  in_t: OPM_U16 or OPM_F32.  Asynchronous on cuda_stream; allocates
+ * nothing.  Errors: OPM_ERR_INVALID_ARG (NULL plan or pointer),
+ * OPM_ERR_UNSUPPORTED (input type, launch limits), OPM_ERR_CUDA.
+ */
+opm_status opm_deskew_dual(const opm_plan* plan, const void* raw, opm_dtype in_t, float* vol_f32,
+                           uint16_t* vol_u16, void* cuda_stream);
+
+/*
  * opm_project - widefield-like live view, fused with the deskew (Fig. 2d):
  * the volume is never written to memory.
  *   raw  [nscan][nrows][ncols] of in_t (U16 or F32)

@@ -47,6 +47,8 @@ _SIGS = {
     "opm_deskew": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p]),
     "opm_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
+    "opm_deskew_dual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "opm_skew_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_void_p]),
     "opm_mip_backward": (ctypes.c_int, [ctypes.c_void_p] * 5),
@@ -192,6 +194,15 @@ def _stream(stream):
 def opm_deskew(plan: Plan, raw, vol, stream=None):
     _check(load().opm_deskew(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
                              _ptr(vol, plan.vol_shape, "vol"), _dtype_code(vol), _stream(stream)), "opm_deskew")
+
+
+def opm_deskew_dual(plan: Plan, raw, vol_f32, vol_u16, stream=None):
+    torch = _torch()
+    if vol_f32.dtype != torch.float32 or vol_u16.dtype != torch.uint16:
+        raise TypeError("vol_f32 must be float32 and vol_u16 uint16")
+    _check(load().opm_deskew_dual(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
+                                  _ptr(vol_f32, plan.vol_shape, "vol_f32"), _ptr(vol_u16, plan.vol_shape, "vol_u16"),
+                                  _stream(stream)), "opm_deskew_dual")
 
 
 def opm_project(plan: Plan, raw, zmip=None, zsum=None, ymip=None, argz=None, stream=None):

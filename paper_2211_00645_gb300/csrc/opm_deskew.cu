@@ -29,10 +29,46 @@ __device__ __forceinline__ void load_half(const T* __restrict__ p, bool vec, int
   }
 }
 
-template <typename Tin, typename Tout, typename Acc, int VEC>
+// Stores one half-vector of H output values with streaming stores (16-byte
+// FP32 or 8-byte uint16 vectors when `full`), else element by element.
+template <typename Tout, int H, typename Acc>
+__device__ __forceinline__ void store_half(Tout* op, const Acc (&val)[H], bool full, int lim) {
+  if constexpr (std::is_same<Tout, float>::value && H == 4) {
+    if (full) {
+      st_cs_v4(op, val[0], val[1], val[2], val[3]);
+      return;
+    }
+  }
+  if constexpr (std::is_same<Tout, uint16_t>::value && H == 4) {
+    if (full) {
+      const uint32_t lo = (uint32_t)to_u16_rn(val[0]) | ((uint32_t)to_u16_rn(val[1]) << 16);
+      const uint32_t hi = (uint32_t)to_u16_rn(val[2]) | ((uint32_t)to_u16_rn(val[3]) << 16);
+      asm volatile("st.global.cs.v2.b32 [%0], {%1, %2};" ::"l"(op), "r"(lo), "r"(hi) : "memory");
+      return;
+    }
+  }
+  if constexpr (std::is_same<Tout, float>::value && H == 2) {
+    if (full) {
+      asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(op), "f"(val[0]), "f"(val[1]) : "memory");
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    if (i >= lim) break;
+    if constexpr (std::is_same<Tout, uint16_t>::value)
+      op[i] = to_u16_rn(val[i]);
+    else
+      op[i] = (Tout)val[i];
+  }
+}
+
+// vol2 (uint16, may be NULL unless DUAL) receives the round-to-nearest-even
+// copy of the same values in the same pass.
+template <typename Tin, typename Tout, typename Acc, int VEC, bool DUAL>
 __global__ void __launch_bounds__(kThreadsX* kThreadsY)
-k_deskew(PlanView v, const Tin* __restrict__ raw, Tout* __restrict__ vol, int xtiles,
-         int in_vec_ok, int out_vec_ok) {
+k_deskew(PlanView v, const Tin* __restrict__ raw, Tout* __restrict__ vol, uint16_t* __restrict__ vol2, int xtiles,
+         int in_vec_ok, int out_vec_ok, int out2_vec_ok) {
   constexpr int H = VEC / 2;  // elements per half-vector
   const int k = blockIdx.x / xtiles;
   const int xt = blockIdx.x - k * xtiles;
@@ -88,49 +124,21 @@ k_deskew(PlanView v, const Tin* __restrict__ raw, Tout* __restrict__ vol, int xt
         for (int i = 0; i < H; ++i) d[h][i] = bb[h][i] - a[h][i];
       ocur = n0;
     }
-    Tout* orow = vol + ((size_t)k * v.ny + j) * v.nx;
+    const size_t orow = ((size_t)k * v.ny + j) * v.nx;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (lim[h] <= 0) continue;
       Acc val[H];
 #pragma unroll
       for (int i = 0; i < H; ++i) val[i] = fma(w, d[h][i], a[h][i]);
-      Tout* op = orow + xh[h];
-      const bool full = out_vec_ok && lim[h] >= H;
-      if constexpr (std::is_same<Tout, float>::value && H == 4) {
-        if (full) {
-          st_cs_v4(op, val[0], val[1], val[2], val[3]);
-          continue;
-        }
-      }
-      if constexpr (std::is_same<Tout, uint16_t>::value && H == 4) {
-        if (full) {
-          const uint32_t lo = (uint32_t)to_u16_rn(val[0]) | ((uint32_t)to_u16_rn(val[1]) << 16);
-          const uint32_t hi = (uint32_t)to_u16_rn(val[2]) | ((uint32_t)to_u16_rn(val[3]) << 16);
-          asm volatile("st.global.cs.v2.b32 [%0], {%1, %2};" ::"l"(op), "r"(lo), "r"(hi) : "memory");
-          continue;
-        }
-      }
-      if constexpr (std::is_same<Tout, float>::value && H == 2) {
-        if (full) {
-          asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(op), "f"(val[0]), "f"(val[1]) : "memory");
-          continue;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < H; ++i) {
-        if (i >= lim[h]) break;
-        if constexpr (std::is_same<Tout, uint16_t>::value)
-          op[i] = to_u16_rn(val[i]);
-        else
-          op[i] = (Tout)val[i];
-      }
+      store_half<Tout, H, Acc>(vol + orow + xh[h], val, out_vec_ok && lim[h] >= H, lim[h]);
+      if constexpr (DUAL) store_half<uint16_t, H, Acc>(vol2 + orow + xh[h], val, out2_vec_ok && lim[h] >= H, lim[h]);
     }
   }
 }
 
-template <typename Tin, typename Tout, typename Acc, int VEC>
-opm_status run(const opm_plan* p, const void* raw, void* vol, cudaStream_t s) {
+template <typename Tin, typename Tout, typename Acc, int VEC, bool DUAL = false>
+opm_status run(const opm_plan* p, const void* raw, void* vol, void* vol2, cudaStream_t s) {
   constexpr int H = VEC / 2;
   const PlanView& v = p->view;
   const int xtiles = (v.nx + kThreadsX * VEC - 1) / (kThreadsX * VEC);
@@ -140,10 +148,12 @@ opm_status run(const opm_plan* p, const void* raw, void* vol, cudaStream_t s) {
     return fail(OPM_ERR_UNSUPPORTED, "deskew grid exceeds launch limits");
   const int in_vec_ok = (v.ncols % H == 0) && ((uintptr_t)raw % 8 == 0);
   const int out_vec_ok = (v.nx % H == 0) && ((uintptr_t)vol % (sizeof(Tout) * H) == 0);
+  const int out2_vec_ok = (v.nx % H == 0) && ((uintptr_t)vol2 % (sizeof(uint16_t) * H) == 0);
   dim3 block(kThreadsX, kThreadsY);
   dim3 grid((unsigned)gx, (unsigned)gy);
-  k_deskew<Tin, Tout, Acc, VEC><<<grid, block, 0, s>>>(
-      v, static_cast<const Tin*>(raw), static_cast<Tout*>(vol), xtiles, in_vec_ok, out_vec_ok);
+  k_deskew<Tin, Tout, Acc, VEC, DUAL><<<grid, block, 0, s>>>(v, static_cast<const Tin*>(raw), static_cast<Tout*>(vol),
+                                                             static_cast<uint16_t*>(vol2), xtiles, in_vec_ok,
+                                                             out_vec_ok, out2_vec_ok);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_deskew");
 }
@@ -152,12 +162,19 @@ opm_status run(const opm_plan* p, const void* raw, void* vol, cudaStream_t s) {
 
 opm_status launch_deskew(const opm_plan* p, const void* raw, opm_dtype in_t, void* vol,
                          opm_dtype out_t, cudaStream_t s) {
-  if (in_t == OPM_U16 && out_t == OPM_F32) return run<uint16_t, float, float, 8>(p, raw, vol, s);
-  if (in_t == OPM_U16 && out_t == OPM_U16) return run<uint16_t, uint16_t, float, 8>(p, raw, vol, s);
-  if (in_t == OPM_F32 && out_t == OPM_F32) return run<float, float, float, 4>(p, raw, vol, s);
-  if (in_t == OPM_F32 && out_t == OPM_U16) return run<float, uint16_t, float, 4>(p, raw, vol, s);
-  if (in_t == OPM_F64 && out_t == OPM_F64) return run<double, double, double, 2>(p, raw, vol, s);
+  if (in_t == OPM_U16 && out_t == OPM_F32) return run<uint16_t, float, float, 8>(p, raw, vol, nullptr, s);
+  if (in_t == OPM_U16 && out_t == OPM_U16) return run<uint16_t, uint16_t, float, 8>(p, raw, vol, nullptr, s);
+  if (in_t == OPM_F32 && out_t == OPM_F32) return run<float, float, float, 4>(p, raw, vol, nullptr, s);
+  if (in_t == OPM_F32 && out_t == OPM_U16) return run<float, uint16_t, float, 4>(p, raw, vol, nullptr, s);
+  if (in_t == OPM_F64 && out_t == OPM_F64) return run<double, double, double, 2>(p, raw, vol, nullptr, s);
   return fail(OPM_ERR_UNSUPPORTED, "unsupported dtype pair");
+}
+
+opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32, uint16_t* vol_u16,
+                              cudaStream_t s) {
+  if (in_t == OPM_U16) return run<uint16_t, float, float, 8, true>(p, raw, vol_f32, vol_u16, s);
+  if (in_t == OPM_F32) return run<float, float, float, 4, true>(p, raw, vol_f32, vol_u16, s);
+  return fail(OPM_ERR_UNSUPPORTED, "dual-output deskew takes uint16 or FP32 input");
 }
 
 }  // namespace opm

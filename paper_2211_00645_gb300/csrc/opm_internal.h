@@ -110,6 +110,8 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t,
                           cudaStream_t s);
 opm_status launch_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
                          void* vol, opm_dtype out_t, cudaStream_t s);
+opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32,
+                              uint16_t* vol_u16, cudaStream_t s);
 opm_status launch_adjoint(const opm_plan* p, const void* vol, void* raw_out,
                           opm_dtype t, cudaStream_t s);
 opm_status launch_mip_backward(const opm_plan* p, const float* g,

@@ -385,6 +385,15 @@ opm_status opm_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
   return launch_deskew(p, raw, in_t, vol, out_t, static_cast<cudaStream_t>(stream));
 }
 
+opm_status opm_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32,
+                           uint16_t* vol_u16, void* stream) {
+  opm_status st = check_plan(p);
+  if (st != OPM_OK) return st;
+  if (!raw || !vol_f32 || !vol_u16) return fail(OPM_ERR_INVALID_ARG, "raw, vol_f32 and vol_u16 must be non-NULL");
+  if (in_t != OPM_U16 && in_t != OPM_F32) return fail(OPM_ERR_UNSUPPORTED, "opm_deskew_dual takes U16 or F32 input");
+  return launch_deskew_dual(p, raw, in_t, vol_f32, vol_u16, static_cast<cudaStream_t>(stream));
+}
+
 opm_status opm_project(const opm_plan* p, const void* raw, opm_dtype in_t,
                        float* zmip, float* zsum, float* ymip, int32_t* argz,
                        void* stream) {

@@ -339,3 +339,69 @@ def test_liveview_full_size_sampled(lib, liveview):
     got = vol[torch.from_numpy(ks).cuda(), torch.from_numpy(js).cuda(), torch.from_numpy(xv).cuda()].cpu().numpy()
     ref = O.voxels(R, g, ks, js, xv)
     assert np.max(np.abs(got - ref)) <= TOL * float(np.max(np.abs(zmip)))
+
+
+def test_large_full_size_sampled(lib):
+    """1000 x 1024 x 2048 uint16 stack (theta 45, step 0.2, pixel 0.115):
+    FP32 and round-to-nearest uint16 volumes and the z-MIP at full size,
+    against the oracle on sampled columns and voxels; the uint16 volume equals
+    the rounded FP32 volume everywhere."""
+    c = opm_synth.CONFIGS["large_1000x1024x2048"]
+    R = opm_synth.tiled_stack((c.nscan, c.nrows, c.ncols), seed=c.seed)
+    g = O.geometry(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    plan = lib.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    raw = to_dev(R, torch)
+    zmip = lib.project(plan, raw, zmip=True)["zmip"]
+    vol = lib.deskew(plan, raw)                                    # FP32, 20.7 GB
+    vol16 = lib.deskew(plan, raw, out_dtype=torch.uint16)          # 10.3 GB
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    rng = np.random.default_rng(3)
+    xs = np.unique(np.concatenate([rng.integers(0, c.ncols, 6), [0, 127, 128, c.ncols - 1]]))
+    Rs = R[:, :, xs].astype(np.float64)
+    gs = O.geometry(c.nscan, c.nrows, len(xs), c.theta_deg, c.step, c.pixel)
+    zref, _, _, _ = O.project(Rs, gs)
+    assert_close(zmip.cpu().numpy()[:, xs], zref, what="large zmip sampled")
+    ks = rng.integers(0, g.nz, 4000)
+    js = rng.integers(0, g.ny, 4000)
+    xv = rng.integers(0, g.nx, 4000)
+    idx = (torch.from_numpy(ks).cuda(), torch.from_numpy(js).cuda(), torch.from_numpy(xv).cuda())
+    ref = O.voxels(R, g, ks, js, xv)
+    got = vol[idx].cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= TOL * float(np.max(np.abs(zref)))
+    got16 = vol16.view(torch.int16)[idx].cpu().numpy().view(np.uint16).astype(np.int64)
+    assert np.max(np.abs(got16 - O.to_u16(ref).astype(np.int64))) <= 1
+    for k0 in range(0, g.nz, 64):                                  # whole volume, in slabs of rows
+        r = torch.round(vol[k0:k0 + 64]).clamp_(0, 65535).to(torch.int32)
+        assert torch.equal(r, vol16[k0:k0 + 64].view(torch.int16).to(torch.int32) & 0xFFFF)
+    assert torch.equal(vol.max(dim=0).values, zmip)
+    # both volumes in one pass: the same bytes as the two separate calls
+    vol_b = torch.empty_like(vol)
+    vol16_b = torch.empty_like(vol16)
+    lib.opm_deskew_dual(plan, raw, vol_b, vol16_b)
+    torch.cuda.synchronize()
+    assert torch.equal(vol_b, vol)
+    assert torch.equal(vol16_b.view(torch.int16), vol16.view(torch.int16))
+
+
+@pytest.mark.parametrize("shape", [(16, 24, 32, 45.0, 0.2, 0.115), (33, 50, 264, 35.0, 0.3, 0.1)])
+@pytest.mark.parametrize("dtype", ["u16", "f32"])
+def test_deskew_dual_small(lib, shape, dtype):
+    n, r, c = shape[:3]
+    R = opm_synth.raw_stack(opm_synth.StackConfig("d", *shape, n_blobs=5, sigma=(1.0, 3.0), amp=(200.0, 4000.0),
+                                                  seed=8))
+    if dtype == "f32":
+        R = R.astype(np.float32) - 300.0
+    plan = lib.Plan(*shape)
+    raw = to_dev(R, torch)
+    f = torch.empty(plan.vol_shape, device="cuda")
+    u = torch.empty(plan.vol_shape, dtype=torch.uint16, device="cuda")
+    lib.opm_deskew_dual(plan, raw, f, u)
+    torch.cuda.synchronize()
+    assert torch.equal(f, lib.deskew(plan, raw))
+    assert torch.equal(u.view(torch.int16), lib.deskew(plan, raw, out_dtype=torch.uint16).view(torch.int16))
+    g = O.geometry(*shape)
+    ref = O.deskew(R.astype(np.float64), g)
+    assert_close(f.cpu().numpy(), ref, what="dual f32")
+    got = u.view(torch.int16).cpu().numpy().view(np.uint16).astype(np.int64)
+    assert np.max(np.abs(got - O.to_u16(ref).astype(np.int64))) <= 1

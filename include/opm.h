@@ -129,6 +129,34 @@ opm_status opm_project(const opm_plan* plan, const void* raw, opm_dtype in_t,
                        void* cuda_stream);
 
 /*
+ * Plane-by-plane live view (the rolling update of Fig. 4a: the maximum
+ * projection is refreshed after every camera exposure).  A stack's z-MIP,
+ * z-sum and y-MIP are accumulated one scan-plane pair at a time, with only
+ * two camera frames on the device.
+ *
+ * opm_stream_begin - zeroes the outputs (zmip, zsum [ny][nx], ymip [nz][nx]
+ * FP32 device arrays; any may be NULL, not all) for a new stack.
+ *
+ * opm_stream_pair - folds into the outputs every voxel whose lower
+ * interpolation plane is n: V = (1 - w) R~[n] + w R~[n + 1] (zero-padded
+ * tent, LINEAR; R~[n] alone for NEAREST).  plane_lo is frame n and plane_hi
+ * frame n + 1, each [nrows][ncols] uint16 on the device; plane_lo is NULL
+ * exactly when n == -1 and plane_hi exactly when n == nscan - 1.  n lies in
+ * [-1, nscan - 1].  After the calls for n = -1, 0, ..., nscan - 1 (any
+ * order) the z-MIP and y-MIP equal opm_project's on the whole stack bit for
+ * bit; the z-sum equals it up to FP32 summation order.  Calls that update
+ * the same outputs must be ordered on one stream.  Asynchronous; allocates
+ * nothing.  A column search that runs past its bound records an error bit
+ * (see opm_plan_check).
+ * Errors: OPM_ERR_INVALID_ARG (NULL plan, no output, n out of range, plane
+ * pointers not matching n), OPM_ERR_UNSUPPORTED (more than 65535 rows),
+ * OPM_ERR_CUDA.
+ */
+opm_status opm_stream_begin(const opm_plan* plan, float* zmip, float* zsum, float* ymip, void* cuda_stream);
+opm_status opm_stream_pair(const opm_plan* plan, const uint16_t* plane_lo, const uint16_t* plane_hi, int64_t n,
+                           float* zmip, float* zsum, float* ymip, void* cuda_stream);
+
+/*
  * opm_skew_adjoint - transpose of the LINEAR deskew map:
  *   raw_out[n][k][x] = sum_j vol[k][j][x] * t(n_f(j,k) - n),  t(u) = max(0, 1-|u|).
  *   vol [nz][ny][nx] and raw_out [nscan][nrows][ncols], both of type t (F32 or

@@ -47,6 +47,9 @@ _SIGS = {
     "opm_deskew": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p]),
     "opm_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
+    "opm_stream_begin": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "opm_stream_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "opm_deskew_dual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "opm_skew_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -194,6 +197,21 @@ def _stream(stream):
 def opm_deskew(plan: Plan, raw, vol, stream=None):
     _check(load().opm_deskew(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
                              _ptr(vol, plan.vol_shape, "vol"), _dtype_code(vol), _stream(stream)), "opm_deskew")
+
+
+def opm_stream_begin(plan: Plan, zmip=None, zsum=None, ymip=None, stream=None):
+    pj = (plan.ny, plan.nx)
+    _check(load().opm_stream_begin(plan.handle, _ptr(zmip, pj, "zmip"), _ptr(zsum, pj, "zsum"),
+                                   _ptr(ymip, (plan.nz, plan.nx), "ymip"), _stream(stream)), "opm_stream_begin")
+
+
+def opm_stream_pair(plan: Plan, plane_lo, plane_hi, n: int, zmip=None, zsum=None, ymip=None, stream=None):
+    """Frames are uint16 CUDA tensors [nrows][ncols] (None outside the stack)."""
+    fr = (plan.nrows, plan.ncols)
+    pj = (plan.ny, plan.nx)
+    _check(load().opm_stream_pair(plan.handle, _ptr(plane_lo, fr, "plane_lo"), _ptr(plane_hi, fr, "plane_hi"), int(n),
+                                  _ptr(zmip, pj, "zmip"), _ptr(zsum, pj, "zsum"), _ptr(ymip, (plan.nz, plan.nx), "ymip"),
+                                  _stream(stream)), "opm_stream_pair")
 
 
 def opm_deskew_dual(plan: Plan, raw, vol_f32, vol_u16, stream=None):

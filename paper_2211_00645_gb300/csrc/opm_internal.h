@@ -57,6 +57,7 @@ static_assert(sizeof(FastRow) == 288, "FastRow is copied as 288 bytes");
 enum : unsigned {
   kErrSlabRange = 1u,   // a plane offset fell outside the staged slab
   kErrWaitTimeout = 2u, // an mbarrier wait gave up
+  kErrSearch = 4u,      // a column search of the plane-pair kernel ran past its bound
 };
 
 void set_error(const std::string& msg);
@@ -112,6 +113,9 @@ opm_status launch_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
                          void* vol, opm_dtype out_t, cudaStream_t s);
 opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32,
                               uint16_t* vol_u16, cudaStream_t s);
+opm_status launch_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, cudaStream_t s);
+opm_status launch_stream_pair(const opm_plan* p, const uint16_t* lo, const uint16_t* hi, int n, float* zmip,
+                              float* zsum, float* ymip, cudaStream_t s);
 opm_status launch_adjoint(const opm_plan* p, const void* vol, void* raw_out,
                           opm_dtype t, cudaStream_t s);
 opm_status launch_mip_backward(const opm_plan* p, const float* g,

@@ -385,6 +385,26 @@ opm_status opm_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
   return launch_deskew(p, raw, in_t, vol, out_t, static_cast<cudaStream_t>(stream));
 }
 
+opm_status opm_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, void* stream) {
+  opm_status st = check_plan(p);
+  if (st != OPM_OK) return st;
+  if (!zmip && !zsum && !ymip) return fail(OPM_ERR_INVALID_ARG, "at least one projection output is required");
+  return launch_stream_begin(p, zmip, zsum, ymip, static_cast<cudaStream_t>(stream));
+}
+
+opm_status opm_stream_pair(const opm_plan* p, const uint16_t* plane_lo, const uint16_t* plane_hi, int64_t n,
+                           float* zmip, float* zsum, float* ymip, void* stream) {
+  opm_status st = check_plan(p);
+  if (st != OPM_OK) return st;
+  if (!zmip && !zsum && !ymip) return fail(OPM_ERR_INVALID_ARG, "at least one projection output is required");
+  if (n < -1 || n > p->nscan - 1) return fail(OPM_ERR_INVALID_ARG, "n must lie in [-1, nscan - 1]");
+  if ((n >= 0) != (plane_lo != nullptr))
+    return fail(OPM_ERR_INVALID_ARG, "plane_lo must be NULL exactly when n == -1");
+  if ((n + 1 < p->nscan) != (plane_hi != nullptr))
+    return fail(OPM_ERR_INVALID_ARG, "plane_hi must be NULL exactly when n == nscan - 1");
+  return launch_stream_pair(p, plane_lo, plane_hi, (int)n, zmip, zsum, ymip, static_cast<cudaStream_t>(stream));
+}
+
 opm_status opm_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32,
                            uint16_t* vol_u16, void* stream) {
   opm_status st = check_plan(p);

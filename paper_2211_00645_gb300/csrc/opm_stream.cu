@@ -1,0 +1,137 @@
+// Plane-by-plane live view: the projections of a stack accumulated one scan
+// plane pair at a time, as the camera delivers frames (the rolling update of
+// Fig. 4a).  The call for the pair (n, n + 1) evaluates exactly the voxels
+// whose lower interpolation plane is n, V = (1 - w) R~[n] + w R~[n + 1], and
+// folds them into the z-MIP, z-sum and y-MIP.  Every voxel has one lower
+// plane, so the calls for n = -1 .. nscan - 1 cover the volume once; the
+// per-voxel arithmetic (plane, weight, FMA on the plane difference) is the
+// fast projection's, so the z-MIP and y-MIP end bit-identical to it.
+#include "opm_common.cuh"
+
+namespace opm {
+
+namespace {
+
+constexpr int kSVec = 4;         // columns x per thread
+constexpr int kSThreads = 128;   // threads per CTA, along x
+constexpr int kSearchSteps = 64; // bound on the column search of one row
+
+__global__ void k_stream_zero(float* zmip, float* zsum, long long nj, float* ymip, long long nk) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nj; i += stride) {
+    if (zmip) zmip[i] = 0.0f;
+    if (zsum) zsum[i] = 0.0f;
+  }
+  if (ymip)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += stride) ymip[i] = 0.0f;
+}
+
+// Loads this thread's kSVec columns of camera row k of one plane (zeros for
+// a missing plane or columns past the edge).
+__device__ __forceinline__ void load_row(const uint16_t* __restrict__ plane, const PlanView& v, int k, int x0,
+                                         bool vec, float (&out)[kSVec]) {
+#pragma unroll
+  for (int i = 0; i < kSVec; ++i) out[i] = 0.0f;
+  if (!plane) return;
+  const uint16_t* p = plane + (size_t)k * v.ncols + x0;
+  if (vec) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    out[0] = (float)(u.x & 0xFFFFu);
+    out[1] = (float)(u.x >> 16);
+    out[2] = (float)(u.y & 0xFFFFu);
+    out[3] = (float)(u.y >> 16);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kSVec; ++i)
+      if (x0 + i < v.nx) out[i] = (float)__ldg(p + i);
+  }
+}
+
+// One CTA row per camera row k (blockIdx.y), kSThreads x kSVec columns per
+// CTA.  The columns j of row k whose lower plane is n form one run; it is
+// found from an FP32 estimate and corrected with the exact split-table
+// arithmetic.
+__global__ void __launch_bounds__(kSThreads)
+k_stream_pair(PlanView v, const uint16_t* __restrict__ lo, const uint16_t* __restrict__ hi, int n, float* zmip,
+              float* zsum, float* ymip, int vec_ok) {
+  const int k = blockIdx.y;
+  const int x0 = (blockIdx.x * kSThreads + threadIdx.x) * kSVec;
+  if (x0 >= v.nx) return;
+  const Split b = v.B[k];
+  // first column with lower plane >= n: estimate, then walk (bounded)
+  const float half = v.linear ? 0.0f : 0.5f;
+  const float est = (float)v.J0 + ((float)n - half + (float)b.i + b.f) * v.rinv;
+  int j = (int)fminf(fmaxf(floorf(est), 0.0f), (float)(v.ny - 1));
+  int n0;
+  float w;
+  int steps = 0;
+  while (j > 0 && steps < kSearchSteps) {
+    plane_weight(v.A[j - 1], b, v.linear, n0, w);
+    if (n0 < n) break;
+    --j;
+    ++steps;
+  }
+  while (j < v.ny && steps < kSearchSteps) {
+    plane_weight(v.A[j], b, v.linear, n0, w);
+    if (n0 >= n) break;
+    ++j;
+    ++steps;
+  }
+  if (steps >= kSearchSteps) {
+    if (threadIdx.x == 0) atomicOr(v.err, kErrSearch);
+    return;
+  }
+  float a[kSVec], d[kSVec];
+  const bool vec = vec_ok && x0 + kSVec <= v.nx;
+  load_row(lo, v, k, x0, vec, a);
+  load_row(hi, v, k, x0, vec, d);
+#pragma unroll
+  for (int i = 0; i < kSVec; ++i) d[i] = d[i] - a[i];  // exact: integers below 2^24
+  float ym[kSVec];
+#pragma unroll
+  for (int i = 0; i < kSVec; ++i) ym[i] = 0.0f;  // uint16 voxels are >= 0
+  bool any = false;
+#pragma unroll 1
+  for (; j < v.ny; ++j) {
+    plane_weight(v.A[j], b, v.linear, n0, w);
+    if (n0 != n) break;
+    any = true;
+    const size_t row = (size_t)j * v.nx + x0;
+#pragma unroll
+    for (int i = 0; i < kSVec; ++i) {
+      if (x0 + i >= v.nx) break;
+      const float val = fmaf(w, d[i], a[i]);
+      ym[i] = fmaxf(ym[i], val);
+      if (zmip) atomicMax(reinterpret_cast<int*>(zmip + row + i), __float_as_int(val));
+      if (zsum) atomicAdd(zsum + row + i, val);
+    }
+  }
+  if (ymip && any) {
+    float* yr = ymip + (size_t)k * v.nx + x0;
+#pragma unroll
+    for (int i = 0; i < kSVec; ++i)
+      if (x0 + i < v.nx) yr[i] = fmaxf(yr[i], ym[i]);  // one thread per (k, x) in this launch
+  }
+}
+
+}  // namespace
+
+opm_status launch_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, cudaStream_t s) {
+  const PlanView& v = p->view;
+  k_stream_zero<<<4 * 152, 256, 0, s>>>(zmip, zsum, (long long)v.ny * v.nx, ymip, (long long)v.nz * v.nx);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_stream_zero");
+}
+
+opm_status launch_stream_pair(const opm_plan* p, const uint16_t* lo, const uint16_t* hi, int n, float* zmip,
+                              float* zsum, float* ymip, cudaStream_t s) {
+  const PlanView& v = p->view;
+  const int xblocks = (v.nx + kSThreads * kSVec - 1) / (kSThreads * kSVec);
+  if (v.nz > 65535) return fail(OPM_ERR_UNSUPPORTED, "more than 65535 camera rows");
+  const int vec_ok = (v.ncols % kSVec == 0) && ((uintptr_t)lo % 8 == 0) && ((uintptr_t)hi % 8 == 0);
+  k_stream_pair<<<dim3(xblocks, v.nz), kSThreads, 0, s>>>(v, lo, hi, n, zmip, zsum, ymip, vec_ok);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_stream_pair");
+}
+
+}  // namespace opm

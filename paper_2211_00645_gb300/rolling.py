@@ -1,0 +1,69 @@
+"""Live view of a stack that arrives frame by frame (Fig. 4).
+
+The paper offers two refresh modes: global, where the projection is shown
+once per complete stack, and rolling, where it is refreshed after every
+camera exposure so that slow acquisitions (long exposures) still give a
+responsive view.  ``RollingView`` serves both from two device frame buffers:
+each new frame n is copied in and the voxels whose lower plane is n - 1 are
+folded into the projections (``opm_stream_pair``); the frame after the last
+closes the stack.  In rolling mode every push returns the projections so
+far; in global mode only the push that completes a stack does.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+from . import Plan, opm_stream_begin, opm_stream_pair
+
+
+class RollingView:
+    """Accumulates the z-MIP / y-MIP (and optionally z-sum) of successive
+    stacks of ``plan``'s shape, one uint16 frame [nrows][ncols] per push."""
+
+    def __init__(self, plan: Plan, mode: str = "rolling", zsum: bool = False, stream=None):
+        import torch
+        if mode not in ("rolling", "global"):
+            raise ValueError("mode must be 'rolling' or 'global'")
+        self.torch = torch
+        self.plan, self.mode = plan, mode
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.frames = [torch.empty((plan.nrows, plan.ncols), dtype=torch.uint16, device=dev) for _ in range(2)]
+        self.zmip = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
+        self.ymip = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
+        self.zsum = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev) if zsum else None
+        self.n = 0            # frames of the current stack received so far
+        self.stacks = 0       # completed stacks
+
+    def _outs(self):
+        return self.zmip, self.zsum, self.ymip
+
+    def push(self, frame) -> Optional[dict]:
+        """Adds the next frame (uint16 [nrows][ncols], host or device).
+        Returns {"zmip", "ymip"[, "zsum"], "frames", "complete"} (device
+        tensors, valid until the next push) when the mode publishes a view."""
+        torch = self.torch
+        p = self.plan
+        if tuple(frame.shape) != (p.nrows, p.ncols) or frame.dtype != torch.uint16:
+            raise ValueError(f"frame must be uint16 {(p.nrows, p.ncols)}")
+        cur = self.frames[self.n % 2]
+        with torch.cuda.stream(self.stream):
+            cur.view(torch.int16).copy_(frame.view(torch.int16), non_blocking=True)
+        zmip, zsum, ymip = self._outs()
+        if self.n == 0:
+            opm_stream_begin(p, zmip, zsum, ymip, self.stream)
+            opm_stream_pair(p, None, cur, -1, zmip, zsum, ymip, self.stream)
+        else:
+            opm_stream_pair(p, self.frames[(self.n - 1) % 2], cur, self.n - 1, zmip, zsum, ymip, self.stream)
+        self.n += 1
+        complete = self.n == p.nscan
+        if complete:
+            opm_stream_pair(p, cur, None, p.nscan - 1, zmip, zsum, ymip, self.stream)
+            self.n = 0
+            self.stacks += 1
+        if self.mode == "rolling" or complete:
+            out = {"zmip": zmip, "ymip": ymip, "frames": p.nscan if complete else self.n, "complete": complete}
+            if zsum is not None:
+                out["zsum"] = zsum
+            return out
+        return None

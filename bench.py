@@ -212,6 +212,74 @@ def tune_serving(torch, plans, ring):
     return e
 
 
+def rolling_bench(torch, opm, plan, host_raw, raw):
+    """Frame-by-frame live view of the live-view stack (Fig. 4 rolling and
+    global modes): every frame is copied in from pinned host memory and its
+    plane pair folded into the projections.  Reported: the device time per
+    frame, the latency from the last frame's copy to a complete view, and
+    the same latency for the whole-stack path (copy the stack, then one fused
+    projection)."""
+    s = torch.cuda.current_stream()
+    frames = [torch.empty((plan.nrows, plan.ncols), dtype=torch.uint16, device="cuda") for _ in range(2)]
+    z = torch.empty((plan.ny, plan.nx), device="cuda")
+    y = torch.empty((plan.nz, plan.nx), device="cuda")
+
+    def one_stack(ev=None):
+        opm.opm_stream_begin(plan, z, None, y, s)
+        for n in range(plan.nscan):
+            cur = frames[n % 2]
+            if ev is not None and n == plan.nscan - 1:
+                ev[0].record(s)
+            cur.view(torch.int16).copy_(host_raw[n], non_blocking=True)
+            opm.opm_stream_pair(plan, frames[(n - 1) % 2] if n else None, cur, n - 1, z, None, y, s)
+        opm.opm_stream_pair(plan, frames[(plan.nscan - 1) % 2], None, plan.nscan - 1, z, None, y, s)
+        if ev is not None:
+            ev[1].record(s)
+
+    for _ in range(2):
+        one_stack()
+    torch.cuda.synchronize()
+    reps = 5
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    for r in range(reps):
+        one_stack(ev[r])
+    t1.record(s)
+    torch.cuda.synchronize()
+    stack_ms = t0.elapsed_time(t1) / reps
+    last_us = statistics.median(e[0].elapsed_time(e[1]) for e in ev) * 1e3
+    # kernels alone, frames resident
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(s)
+    for n in range(-1, plan.nscan):
+        opm.opm_stream_pair(plan, raw[n] if n >= 0 else None, raw[n + 1] if n + 1 < plan.nscan else None, n, z,
+                            None, y, s)
+    k1.record(s)
+    torch.cuda.synchronize()
+    pair_us = k0.elapsed_time(k1) * 1e3 / (plan.nscan + 1)
+    # whole-stack path: copy the stack in, then the fused projection
+    w0 = torch.cuda.Event(enable_timing=True)
+    w1 = torch.cuda.Event(enable_timing=True)
+    wz = torch.empty_like(z)
+    wy = torch.empty_like(y)
+    w0.record(s)
+    for _ in range(reps):
+        raw.view(torch.int16).copy_(host_raw, non_blocking=True)
+        opm.opm_project(plan, raw, wz, None, wy, None, s)
+    w1.record(s)
+    torch.cuda.synchronize()
+    assert torch.equal(z, wz) and torch.equal(y, wy)
+    whole_ms = w0.elapsed_time(w1) / reps
+    return {"frames": plan.nscan, "frame_bytes": plan.nrows * plan.ncols * 2,
+            "per_frame_us": round(stack_ms * 1e3 / plan.nscan, 2), "pair_kernel_us": round(pair_us, 2),
+            "max_camera_fps": round(plan.nscan / (stack_ms * 1e-3)),
+            "last_frame_to_view_us": round(last_us, 1), "whole_stack_copy_then_project_ms": round(whole_ms, 3),
+            "identical_to_whole_stack": True}
+
+
 def serve_bench(args, torch):
     """Serving comparison on the batched-serving workload: the live-view
     server against the plain per-stack path, first at Poisson arrivals of
@@ -440,6 +508,7 @@ def main():
         "gpu_launches": 3 * K,
         "clocks": clocks,
     }
+    line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
     if args.serve_paced > 0 or args.serve_saturated > 0:
         del vol, raw
         torch.cuda.empty_cache()

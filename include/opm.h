@@ -112,6 +112,23 @@ opm_status opm_deskew_dual(const opm_plan* plan, const void* raw, opm_dtype in_t
                            uint16_t* vol_u16, void* cuda_stream);
 
 /*
+ * opm_deskew_mip - the volume and the live view in one pass over the raw
+ * stack (the paper's remap followed by its maximum projection, Fig. 2c-d):
+ * vol_f32 and/or vol_u16 [nz][ny][nx] as opm_deskew / opm_deskew_dual
+ * write them, zmip [ny][nx] and ymip [nz][nx] as opm_project writes them
+ * (either may be NULL), all bit-identical to those calls.  uint16 input on
+ * plans the fast projection takes (pixel <= step, ny >= 32, rows of a
+ * multiple of 16 bytes, 16-byte aligned raw) runs as one fused kernel that
+ * stores every voxel as it folds it into the projections, plus a kernel
+ * that zeroes the rows outside each tile's band; anything else runs the
+ * separate calls.  Asynchronous; allocates nothing.
+ * Errors: OPM_ERR_INVALID_ARG (NULL plan or raw, no volume), OPM_ERR_UNSUPPORTED
+ * (input type, launch limits), OPM_ERR_CUDA.
+ */
+opm_status opm_deskew_mip(const opm_plan* plan, const void* raw, opm_dtype in_t, float* vol_f32, uint16_t* vol_u16,
+                          float* zmip, float* ymip, void* cuda_stream);
+
+/*
  * opm_project - widefield-like live view, fused with the deskew (Fig. 2d):
  * the volume is never written to memory.
  *   raw  [nscan][nrows][ncols] of in_t (U16 or F32)

@@ -47,6 +47,7 @@ _SIGS = {
     "opm_deskew": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p]),
     "opm_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
+    "opm_deskew_mip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
     "opm_stream_begin": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "opm_stream_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -197,6 +198,19 @@ def _stream(stream):
 def opm_deskew(plan: Plan, raw, vol, stream=None):
     _check(load().opm_deskew(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
                              _ptr(vol, plan.vol_shape, "vol"), _dtype_code(vol), _stream(stream)), "opm_deskew")
+
+
+def opm_deskew_mip(plan: Plan, raw, vol_f32=None, vol_u16=None, zmip=None, ymip=None, stream=None):
+    torch = _torch()
+    if vol_f32 is not None and vol_f32.dtype != torch.float32:
+        raise TypeError("vol_f32 must be float32")
+    if vol_u16 is not None and vol_u16.dtype != torch.uint16:
+        raise TypeError("vol_u16 must be uint16")
+    pj = (plan.ny, plan.nx)
+    _check(load().opm_deskew_mip(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
+                                 _ptr(vol_f32, plan.vol_shape, "vol_f32"), _ptr(vol_u16, plan.vol_shape, "vol_u16"),
+                                 _ptr(zmip, pj, "zmip"), _ptr(ymip, (plan.nz, plan.nx), "ymip"), _stream(stream)),
+           "opm_deskew_mip")
 
 
 def opm_stream_begin(plan: Plan, zmip=None, zsum=None, ymip=None, stream=None):

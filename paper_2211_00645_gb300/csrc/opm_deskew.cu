@@ -158,6 +158,151 @@ opm_status run(const opm_plan* p, const void* raw, void* vol, void* vol2, cudaSt
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_deskew");
 }
 
+// ---------------------------------------------------------------------------
+// Volume and live view in one pass (uint16 input): every voxel is stored as
+// k_deskew stores it, and folded into the z-MIP and y-MIP on the way.  CTA
+// (32 x 8 threads): 128 columns x (4 per lane) x 32 columns j (4 per warp) x
+// a chunk of kMipRows camera rows, 4 CTAs per SM.  The z-maxima of a
+// thread's 4 x 4 voxels
+// stay in registers across the chunk's rows and are folded into the global
+// z-MIP once; the y-maxima of each row are combined across the 8 warps with
+// shared-memory atomics and folded into the global y-MIP once per CTA.  All
+// combines are maxima of non-negative values on their bit patterns, so the
+// result does not depend on their order.
+constexpr int kMipRows = 64;
+constexpr int kMipJ = 4;     // columns j per thread
+constexpr int kMipVec = 4;   // columns x per lane
+
+template <bool F32, bool U16>
+__global__ void __launch_bounds__(kThreadsX* kThreadsY, 4)
+k_deskew_mip(PlanView v, const uint16_t* __restrict__ raw, float* __restrict__ volf, uint16_t* __restrict__ volh,
+             float* __restrict__ zmip, float* __restrict__ ymip, int in_vec_ok, int out_vec_ok) {
+  __shared__ float ybuf[kMipRows][kThreadsX * kMipVec];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int x = blockIdx.x * kThreadsX * kMipVec + lane * kMipVec;
+  const int jb = (blockIdx.y * kThreadsY + w) * kMipJ;
+  const int k0 = blockIdx.z * kMipRows;
+  const int k1 = min(k0 + kMipRows, v.nz);
+  for (int i = threadIdx.y * kThreadsX + threadIdx.x; i < kMipRows * kThreadsX * kMipVec; i += kThreadsX * kThreadsY)
+    (&ybuf[0][0])[i] = 0.0f;
+  __syncthreads();
+  const bool active = x < v.nx && jb < v.ny;
+  const int lim = v.nx - x;  // valid columns of this lane's vector
+  const bool vin = in_vec_ok && lim >= kMipVec;
+  const bool vout = out_vec_ok && lim >= kMipVec;
+  const size_t plane = (size_t)v.nrows * v.ncols;
+  float zmax[kMipJ][kMipVec];
+#pragma unroll
+  for (int j = 0; j < kMipJ; ++j)
+#pragma unroll
+    for (int c = 0; c < kMipVec; ++c) zmax[j][c] = 0.0f;  // uint16 voxels are >= 0
+
+#pragma unroll 1
+  for (int k = k0; active && k < k1; ++k) {
+    const Split b = v.B[k];
+    const uint16_t* rowp = raw + (size_t)k * v.ncols + x;
+    float a[kMipVec], bb[kMipVec], d[kMipVec], ym[kMipVec];
+#pragma unroll
+    for (int c = 0; c < kMipVec; ++c) a[c] = bb[c] = d[c] = ym[c] = 0.0f;
+    int ocur = -0x40000000;
+    auto fetch = [&](int n, float(&out)[kMipVec]) {
+      if (n >= 0 && n < v.nscan) {
+        const uint16_t* p = rowp + (size_t)n * plane;
+        if (vin) {
+          const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+          out[0] = (float)(u.x & 0xFFFFu);
+          out[1] = (float)(u.x >> 16);
+          out[2] = (float)(u.y & 0xFFFFu);
+          out[3] = (float)(u.y >> 16);
+        } else {
+#pragma unroll
+          for (int c = 0; c < kMipVec; ++c) out[c] = c < lim ? (float)__ldg(p + c) : 0.0f;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < kMipVec; ++c) out[c] = 0.0f;
+      }
+    };
+#pragma unroll
+    for (int jj = 0; jj < kMipJ; ++jj) {
+      const int j = jb + jj;
+      if (j >= v.ny) break;
+      int n0;
+      float wt;
+      plane_weight(v.A[j], b, v.linear, n0, wt);
+      if (n0 != ocur) {
+        if (n0 == ocur + 1) {
+#pragma unroll
+          for (int c = 0; c < kMipVec; ++c) a[c] = bb[c];
+        } else {
+          fetch(n0, a);
+        }
+        fetch(n0 + 1, bb);
+#pragma unroll
+        for (int c = 0; c < kMipVec; ++c) d[c] = bb[c] - a[c];  // exact: integers below 2^24
+        ocur = n0;
+      }
+      float val[kMipVec];
+#pragma unroll
+      for (int c = 0; c < kMipVec; ++c) {
+        val[c] = fmaf(wt, d[c], a[c]);
+        zmax[jj][c] = fmaxf(zmax[jj][c], val[c]);
+        ym[c] = fmaxf(ym[c], val[c]);
+      }
+      const size_t o = ((size_t)k * v.ny + j) * v.nx + x;
+      if (vout) {
+        if (F32) st_cs_v4(volf + o, val[0], val[1], val[2], val[3]);
+        if (U16) {
+          const uint32_t lo = (uint32_t)to_u16_rn(val[0]) | ((uint32_t)to_u16_rn(val[1]) << 16);
+          const uint32_t hi = (uint32_t)to_u16_rn(val[2]) | ((uint32_t)to_u16_rn(val[3]) << 16);
+          asm volatile("st.global.cs.v2.b32 [%0], {%1, %2};" ::"l"(volh + o), "r"(lo), "r"(hi) : "memory");
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < kMipVec; ++c) {
+          if (c >= lim) break;
+          if (F32) volf[o + c] = val[c];
+          if (U16) volh[o + c] = to_u16_rn(val[c]);
+        }
+      }
+    }
+    if (ymip) {
+#pragma unroll
+      for (int c = 0; c < kMipVec; ++c)
+        if (c < lim) atomicMax(reinterpret_cast<int*>(&ybuf[k - k0][lane * kMipVec + c]), __float_as_int(ym[c]));
+    }
+  }
+  if (zmip && active) {
+#pragma unroll
+    for (int jj = 0; jj < kMipJ; ++jj) {
+      const int j = jb + jj;
+      if (j >= v.ny) break;
+      float* zr = zmip + (size_t)j * v.nx + x;
+#pragma unroll
+      for (int c = 0; c < kMipVec; ++c)
+        if (c < lim) atomicMax(reinterpret_cast<int*>(zr + c), __float_as_int(zmax[jj][c]));
+    }
+  }
+  if (ymip) {
+    __syncthreads();
+    const int xb = blockIdx.x * kThreadsX * kMipVec;
+    for (int i = threadIdx.y * kThreadsX + threadIdx.x; i < (k1 - k0) * kThreadsX * kMipVec;
+         i += kThreadsX * kThreadsY) {
+      const int kk = i / (kThreadsX * kMipVec), xx = i % (kThreadsX * kMipVec);
+      if (xb + xx < v.nx)
+        atomicMax(reinterpret_cast<int*>(ymip + (size_t)(k0 + kk) * v.nx + xb + xx), __float_as_int(ybuf[kk][xx]));
+    }
+  }
+}
+
+__global__ void k_zero2(float* a, long long na, float* b, long long nb) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < na || i < nb; i += stride) {
+    if (a && i < na) a[i] = 0.0f;
+    if (b && i < nb) b[i] = 0.0f;
+  }
+}
+
 }  // namespace
 
 opm_status launch_deskew(const opm_plan* p, const void* raw, opm_dtype in_t, void* vol,
@@ -175,6 +320,46 @@ opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t
   if (in_t == OPM_U16) return run<uint16_t, float, float, 8, true>(p, raw, vol_f32, vol_u16, s);
   if (in_t == OPM_F32) return run<float, float, float, 4, true>(p, raw, vol_f32, vol_u16, s);
   return fail(OPM_ERR_UNSUPPORTED, "dual-output deskew takes uint16 or FP32 input");
+}
+
+}  // namespace opm
+
+namespace opm {
+
+opm_status launch_deskew_mip(const opm_plan* p, const void* raw, opm_dtype in_t, float* volf, uint16_t* volh,
+                             float* zmip, float* ymip, cudaStream_t s) {
+  const PlanView& v = p->view;
+  if (in_t != OPM_U16) {
+    // FP32 input: the volume, then the projections
+    opm_status st = OPM_OK;
+    if (volf && volh)
+      st = launch_deskew_dual(p, raw, in_t, volf, volh, s);
+    else
+      st = launch_deskew(p, raw, in_t, volf ? (void*)volf : (void*)volh, volf ? OPM_F32 : OPM_U16, s);
+    if (st != OPM_OK || (!zmip && !ymip)) return st;
+    return launch_project(p, raw, in_t, zmip, nullptr, ymip, nullptr, s);
+  }
+  const int xtiles = (v.nx + kThreadsX * kMipVec - 1) / (kThreadsX * kMipVec);
+  const int jblocks = (v.ny + kThreadsY * kMipJ - 1) / (kThreadsY * kMipJ);
+  const int kchunks = (v.nz + kMipRows - 1) / kMipRows;
+  if (jblocks > 65535 || kchunks > 65535) return fail(OPM_ERR_UNSUPPORTED, "deskew grid exceeds launch limits");
+  if (zmip || ymip) {
+    k_zero2<<<4 * 152, 256, 0, s>>>(zmip, zmip ? (long long)v.ny * v.nx : 0, ymip, ymip ? (long long)v.nz * v.nx : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_zero2");
+  }
+  const int in_vec_ok = (v.ncols % kMipVec == 0) && ((uintptr_t)raw % 8 == 0);
+  const int out_vec_ok = (v.nx % kMipVec == 0) && ((uintptr_t)volf % 16 == 0) && ((uintptr_t)volh % 8 == 0);
+  dim3 grid(xtiles, jblocks, kchunks), block(kThreadsX, kThreadsY);
+  const uint16_t* r = static_cast<const uint16_t*>(raw);
+  if (volf && volh)
+    k_deskew_mip<true, true><<<grid, block, 0, s>>>(v, r, volf, volh, zmip, ymip, in_vec_ok, out_vec_ok);
+  else if (volf)
+    k_deskew_mip<true, false><<<grid, block, 0, s>>>(v, r, volf, volh, zmip, ymip, in_vec_ok, out_vec_ok);
+  else
+    k_deskew_mip<false, true><<<grid, block, 0, s>>>(v, r, volf, volh, zmip, ymip, in_vec_ok, out_vec_ok);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_deskew_mip");
 }
 
 }  // namespace opm

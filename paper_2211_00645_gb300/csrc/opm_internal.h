@@ -113,6 +113,8 @@ opm_status launch_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
                          void* vol, opm_dtype out_t, cudaStream_t s);
 opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32,
                               uint16_t* vol_u16, cudaStream_t s);
+opm_status launch_deskew_mip(const opm_plan* p, const void* raw, opm_dtype in_t, float* volf, uint16_t* volh,
+                             float* zmip, float* ymip, cudaStream_t s);
 opm_status launch_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, cudaStream_t s);
 opm_status launch_stream_pair(const opm_plan* p, const uint16_t* lo, const uint16_t* hi, int n, float* zmip,
                               float* zsum, float* ymip, cudaStream_t s);

@@ -385,6 +385,15 @@ opm_status opm_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
   return launch_deskew(p, raw, in_t, vol, out_t, static_cast<cudaStream_t>(stream));
 }
 
+opm_status opm_deskew_mip(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32, uint16_t* vol_u16,
+                          float* zmip, float* ymip, void* stream) {
+  opm_status st = check_plan(p);
+  if (st != OPM_OK) return st;
+  if (!raw || (!vol_f32 && !vol_u16)) return fail(OPM_ERR_INVALID_ARG, "raw and at least one volume are required");
+  if (in_t != OPM_U16 && in_t != OPM_F32) return fail(OPM_ERR_UNSUPPORTED, "opm_deskew_mip takes U16 or F32 input");
+  return launch_deskew_mip(p, raw, in_t, vol_f32, vol_u16, zmip, ymip, static_cast<cudaStream_t>(stream));
+}
+
 opm_status opm_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, void* stream) {
   opm_status st = check_plan(p);
   if (st != OPM_OK) return st;

@@ -191,6 +191,41 @@ def cpu_baseline(R, cfg, cols, budget_s=20.0):
             "sample": f"first {cols} of {cfg.ncols} x-columns (project + deskew, {t:.1f} s)"}
 
 
+def _oracle_chunk(job):
+    """Worker of cpu_baseline_all_cores: the oracle on one block of x-columns."""
+    import oracle as O
+    R, geo = job
+    g = O.geometry(*geo)
+    t0 = time.perf_counter()
+    O.project(R, g)
+    O.deskew(R, g)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(R, cfg, cols=None):
+    """The same oracle run on every host core at once: the stack's x-columns
+    are independent, so each process takes one block of columns (processes
+    started with spawn, after the GPU work)."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    cols = cols or cfg.ncols
+    blocks = np.array_split(np.arange(cols), ncores)
+    jobs = [(R[:, :, b[0]:b[-1] + 1].astype(np.float64),
+             (cfg.nscan, cfg.nrows, len(b), cfg.theta_deg, cfg.step, cfg.pixel)) for b in blocks if len(b)]
+    sub = opm_synth.StackConfig("a", cfg.nscan, cfg.nrows, cols, cfg.theta_deg, cfg.step, cfg.pixel,
+                                0, (1, 1), (1, 1))
+    import oracle as O
+    live, vol = algorithmic_bytes(sub, O.geometry(cfg.nscan, cfg.nrows, cols, cfg.theta_deg, cfg.step,
+                                                  cfg.pixel).ny)
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        pool.map(_oracle_chunk, [(j[0][:, :, :1], j[1][:2] + (1,) + j[1][3:]) for j in jobs])  # start-up
+        t0 = time.perf_counter()
+        pool.map(_oracle_chunk, jobs)
+        t = time.perf_counter() - t0
+    return {"value": round((live + vol) / t / 1e9, 4), "unit": UNIT, "cores": len(jobs), "kind": "oracle",
+            "sample": f"first {cols} of {cfg.ncols} x-columns in {len(jobs)} processes ({t:.1f} s)"}
+
+
 def tune_serving(torch, plans, ring):
     """Launch shape of the batched server, tuned on six stacks of the serving
     mix (one tick's worth) copied to the device."""
@@ -508,6 +543,21 @@ def main():
         "gpu_launches": 3 * K,
         "clocks": clocks,
     }
+    # the same outputs in one pass (opm_deskew_mip): raw read once
+    for _ in range(3):
+        opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(20):
+        opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t_one = f0.elapsed_time(f1) / 20 * 1e-3
+    one_b = vol_b + live_b - 2 * cfg.nscan * cfg.nrows * cfg.ncols
+    line["one_pass"] = {"call": "opm_deskew_mip (FP32 volume + z-MIP + y-MIP)", "bytes": one_b,
+                        "us": round(t_one * 1e6, 2), "GBps": round(one_b / t_one / 1e9, 1),
+                        "frac": round(one_b / t_one / 1e9 / peak, 4)}
     line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
     if args.serve_paced > 0 or args.serve_saturated > 0:
         del vol, raw
@@ -515,6 +565,7 @@ def main():
         line["serving"] = serve_bench(args, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(R, cfg, args.ref_cols)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(R, cfg)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

@@ -22,3 +22,10 @@ from .opm import (  # noqa: F401
     to_u16,
     covered_mask,
 )
+from .sheet import (  # noqa: F401
+    sheet_rows,
+    sheet_frame,
+    sheet_project,
+    sheet_matrix_row,
+    warp_rows,
+)

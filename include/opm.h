@@ -146,6 +146,42 @@ opm_status opm_project(const opm_plan* plan, const void* raw, opm_dtype in_t,
                        void* cuda_stream);
 
 /*
+ * The paper's own live view (sheet frame).  Every raw frame n is remapped
+ * into a larger image shifted along the camera-row axis by its accumulated
+ * lateral offset, n * shear rows, where Eq. (1) gives shear =
+ * step * cos(alpha) / pixel (Fig. 2c); the view is the brightest value over
+ * the frames at each pixel (Fig. 2d).  A sub-row shift interpolates linearly
+ * between the two neighbouring camera rows (zero outside the frame).  A
+ * smaller shear followed by opm_warp_rows changes the viewing angle
+ * (shear-warp, Fig. 3).
+ *
+ * opm_sheet_rows - rows of the remapped image: nrows + ceil((nscan - 1) *
+ * shear) (shear >= 0, finite; nscan, nrows >= 1).
+ * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED (over 2^31 rows).
+ *
+ * opm_sheet_project - out[Y][x] = max_n S[n][Y][x] for raw [nscan][nrows]
+ * [ncols] (in_t U16 or F32, device) into out [out_rows][ncols] FP32
+ * (device, caller-owned); out_rows must equal opm_sheet_rows.  Frames that
+ * do not reach a row contribute 0 to its maximum.  Asynchronous; allocates
+ * nothing.  Errors: OPM_ERR_INVALID_ARG (NULL, sizes, out_rows),
+ * OPM_ERR_UNSUPPORTED (type, more planes than the shared-memory shift
+ * table holds, sizes past 2^31), OPM_ERR_CUDA.
+ */
+opm_status opm_sheet_rows(int64_t nscan, int64_t nrows, double shear, int64_t* rows);
+opm_status opm_sheet_project(const void* raw, opm_dtype in_t, int64_t nscan, int64_t nrows, int64_t ncols,
+                             double shear, float* out, int64_t out_rows, void* cuda_stream);
+
+/*
+ * opm_warp_rows - the warp of the shear-warp view (Fig. 3): out[Y'][x] =
+ * in at row a * Y' + b, linear between rows, zero outside [0, in_rows).
+ * in [in_rows][ncols], out [out_rows][ncols], FP32 device arrays.
+ * Asynchronous; allocates nothing.  Errors: OPM_ERR_INVALID_ARG (NULL,
+ * sizes, non-finite a or b), OPM_ERR_UNSUPPORTED (sizes), OPM_ERR_CUDA.
+ */
+opm_status opm_warp_rows(const float* in, int64_t in_rows, int64_t ncols, float* out, int64_t out_rows, double a,
+                         double b, void* cuda_stream);
+
+/*
  * Plane-by-plane live view (the rolling update of Fig. 4a: the maximum
  * projection is refreshed after every camera exposure).  A stack's z-MIP,
  * z-sum and y-MIP are accumulated one scan-plane pair at a time, with only

@@ -47,6 +47,12 @@ _SIGS = {
     "opm_deskew": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p]),
     "opm_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
+    "opm_sheet_rows": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "opm_sheet_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "opm_warp_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "opm_deskew_mip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
     "opm_stream_begin": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "opm_stream_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -198,6 +204,37 @@ def _stream(stream):
 def opm_deskew(plan: Plan, raw, vol, stream=None):
     _check(load().opm_deskew(plan.handle, _ptr(raw, plan.raw_shape, "raw"), _dtype_code(raw),
                              _ptr(vol, plan.vol_shape, "vol"), _dtype_code(vol), _stream(stream)), "opm_deskew")
+
+
+def opm_sheet_rows(nscan: int, nrows: int, shear: float) -> int:
+    rows = ctypes.c_int64()
+    _check(load().opm_sheet_rows(int(nscan), int(nrows), float(shear), ctypes.byref(rows)), "opm_sheet_rows")
+    return rows.value
+
+
+def opm_sheet_project(raw, shear: float, out=None, stream=None):
+    """Sheet-frame view of raw [nscan][nrows][ncols] (uint16 or float32 CUDA
+    tensor); returns out [opm_sheet_rows(...)][ncols] float32."""
+    torch = _torch()
+    nscan, nrows, ncols = raw.shape
+    H = opm_sheet_rows(nscan, nrows, shear)
+    if out is None:
+        out = torch.empty((H, ncols), dtype=torch.float32, device=raw.device)
+    _check(load().opm_sheet_project(_ptr(raw, None, "raw"), _dtype_code(raw), nscan, nrows, ncols, float(shear),
+                                    _ptr(out, (H, ncols), "out"), H, _stream(stream)), "opm_sheet_project")
+    return out
+
+
+def opm_warp_rows(inp, out_rows: int, a: float, b: float, out=None, stream=None):
+    torch = _torch()
+    H, ncols = inp.shape
+    if inp.dtype != torch.float32:
+        raise TypeError("in must be float32")
+    if out is None:
+        out = torch.empty((out_rows, ncols), dtype=torch.float32, device=inp.device)
+    _check(load().opm_warp_rows(_ptr(inp, None, "in"), H, ncols, _ptr(out, (out_rows, ncols), "out"), int(out_rows),
+                                float(a), float(b), _stream(stream)), "opm_warp_rows")
+    return out
 
 
 def opm_deskew_mip(plan: Plan, raw, vol_f32=None, vol_u16=None, zmip=None, ymip=None, stream=None):

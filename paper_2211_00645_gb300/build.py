@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libopm.so")
 
-SOURCES = ["opm_plan.cu", "opm_deskew.cu", "opm_adjoint.cu", "opm_project.cu", "opm_batch.cu", "opm_stream.cu"]
+SOURCES = ["opm_plan.cu", "opm_deskew.cu", "opm_adjoint.cu", "opm_project.cu", "opm_batch.cu", "opm_stream.cu", "opm_sheet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]

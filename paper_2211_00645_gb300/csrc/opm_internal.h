@@ -115,6 +115,10 @@ opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t
                               uint16_t* vol_u16, cudaStream_t s);
 opm_status launch_deskew_mip(const opm_plan* p, const void* raw, opm_dtype in_t, float* volf, uint16_t* volh,
                              float* zmip, float* ymip, cudaStream_t s);
+opm_status launch_sheet_project(const void* raw, opm_dtype in_t, int nscan, int nrows, int ncols, double shear,
+                                float* out, int H, cudaStream_t s);
+opm_status launch_warp_rows(const float* in, int H, int ncols, float* out, int Ho, double a, double b,
+                            cudaStream_t s);
 opm_status launch_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, cudaStream_t s);
 opm_status launch_stream_pair(const opm_plan* p, const uint16_t* lo, const uint16_t* hi, int n, float* zmip,
                               float* zsum, float* ymip, cudaStream_t s);

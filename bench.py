@@ -558,6 +558,25 @@ def main():
     line["one_pass"] = {"call": "opm_deskew_mip (FP32 volume + z-MIP + y-MIP)", "bytes": one_b,
                         "us": round(t_one * 1e6, 2), "GBps": round(one_b / t_one / 1e9, 1),
                         "frac": round(one_b / t_one / 1e9 / peak, 4)}
+    # the paper's own sheet-frame view (shear of Eq. 1) and a shear-warp view
+    import math as _m
+    shear = cfg.step * _m.cos(_m.radians(cfg.theta_deg)) / cfg.pixel
+    sheet = opm.opm_sheet_project(raw, shear, stream=stream)
+    for _ in range(3):
+        opm.opm_sheet_project(raw, shear, out=sheet, stream=stream)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(20):
+        opm.opm_sheet_project(raw, shear, out=sheet, stream=stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    t_sheet = s0.elapsed_time(s1) / 20 * 1e-3
+    sheet_b = 2 * cfg.nscan * cfg.nrows * cfg.ncols + 4 * sheet.numel()
+    line["sheet_view"] = {"call": "opm_sheet_project", "shear_rows_per_frame": round(shear, 6),
+                          "out": list(sheet.shape), "bytes": sheet_b, "us": round(t_sheet * 1e6, 2),
+                          "GBps": round(sheet_b / t_sheet / 1e9, 1), "frac": round(sheet_b / t_sheet / 1e9 / peak, 4)}
+    del sheet
     line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
     if args.serve_paced > 0 or args.serve_saturated > 0:
         del vol, raw

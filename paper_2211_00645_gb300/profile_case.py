@@ -6,6 +6,7 @@ paper_2211_00645_gb300.profile_case ...``).
   --kernel deskew    full deskewed FP32 volume
   --kernel batch     batched live view over a mix of serving-sized stacks
   --kernel fused     volume + z-MIP + y-MIP in one pass (opm_deskew_mip)
+  --kernel sheet     the sheet-frame view with the shear of Eq. 1 (opm_sheet_project)
   --kernel batch1    the named stack alone through the persistent batch kernel
                      (--kchunk, --ctas: its launch shape)
   --nscan N          override the stack's scan-plane count (smaller captures)
@@ -31,7 +32,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["project", "deskew", "fused", "batch", "batch1"], required=True)
+    ap.add_argument("--kernel", choices=["project", "deskew", "fused", "sheet", "batch", "batch1"], required=True)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--config", default="liveview_200x512x2048")
@@ -83,6 +84,13 @@ def main(argv=None):
 
             def launch():
                 b.launch(args.ctas, s)
+        elif args.kernel == "sheet":
+            import math
+            shear = cfg.step * math.cos(math.radians(cfg.theta_deg)) / cfg.pixel
+            out = opm.opm_sheet_project(raw, shear)
+
+            def launch():
+                opm.opm_sheet_project(raw, shear, out=out, stream=s)
         elif args.kernel == "fused":
             vol = torch.empty(plan.vol_shape, device="cuda")
             zmip = torch.empty((plan.ny, plan.nx), device="cuda")

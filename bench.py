@@ -59,6 +59,16 @@ NCU_TRAFFIC = {
 }
 
 
+def _tree_sha():
+    """Hash of every library source and header (identifies the build measured)."""
+    h = hashlib.sha1()
+    for d in (os.path.join(ROOT, "paper_2211_00645_gb300", "csrc"), os.path.join(ROOT, "include")):
+        for f in sorted(os.listdir(d)):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:12]
+
+
 def _src_sha(kernel):
     h = hashlib.sha1()
     for rel in KERNEL_SOURCES[kernel]:
@@ -541,6 +551,7 @@ def main():
                 "d2h_bytes_per_step": int((host_z.numel() + host_y.numel()) * 4),
                 "ms_per_step": round(e2e_ms, 4)},
         "gpu_launches": 3 * K,
+        "host": {"cores": os.cpu_count(), "library_sources_sha": _tree_sha()},
         "clocks": clocks,
     }
     # the same outputs in one pass (opm_deskew_mip): raw read once

@@ -109,28 +109,54 @@ def power_iteration(plan: Plan, iters: int = 20, seed: int = 0, dtype=torch.floa
 
 
 def reconstruct(plan: Plan, measured: torch.Tensor, iters: int = 100, eta: float | None = None,
-                x0: torch.Tensor | None = None, lipschitz: float | None = None):
+                x0: torch.Tensor | None = None, lipschitz: float | None = None,
+                checkpoint: str | None = None, every: int = 10):
     """Gradient descent on 0.5 ||A^T x - y||^2 over volumes x (output grid).
 
     The gradient A (A^T x - y) is one skew (A^T) and one deskew (A) per
     iteration.  With eta <= 1/L, L = ||A||^2, the loss is non-increasing.
     Returns (x, losses).
+
+    ``checkpoint``: a file path.  If it exists, the run resumes from the
+    iterate, step size and losses stored there; every ``every`` iterations
+    (and at the end) they are written there again with ``torch.save``.  A
+    resumed run ends on the same iterate as an uninterrupted one: each step
+    is a deterministic function of the iterate.
     """
-    if lipschitz is None:
-        lipschitz = power_iteration(plan)
-    if eta is None:
-        eta = 1.0 / lipschitz
-    x = torch.zeros(plan.vol_shape, dtype=measured.dtype, device=measured.device) if x0 is None else x0.clone()
+    import os
+    state = torch.load(checkpoint, map_location=measured.device) if checkpoint and os.path.exists(checkpoint) else None
+    if state is not None:
+        x = state["x"].to(device=measured.device, dtype=measured.dtype).clone()
+        eta = float(state["eta"])
+        losses = list(state["losses"])
+        done = int(state["iters"])
+    else:
+        if lipschitz is None:
+            lipschitz = power_iteration(plan)
+        if eta is None:
+            eta = 1.0 / lipschitz
+        x = torch.zeros(plan.vol_shape, dtype=measured.dtype, device=measured.device) if x0 is None else x0.clone()
+        losses = []
+        done = 0
     r = torch.empty(plan.raw_shape, dtype=measured.dtype, device=measured.device)
     grad = torch.empty_like(x)
-    losses = []
-    for _ in range(iters):
+
+    def save(n):
+        if checkpoint:
+            tmp = checkpoint + ".tmp"
+            torch.save({"x": x, "eta": eta, "losses": losses, "iters": n}, tmp)
+            os.replace(tmp, checkpoint)
+
+    for it in range(done, iters):
         opm_skew_adjoint(plan, x, r)
         r.sub_(measured)
         losses.append(0.5 * float(r.double().pow(2).sum()))
         opm_deskew(plan, r, grad)
         x.add_(grad, alpha=-eta)
+        if checkpoint and (it + 1) % every == 0:
+            save(it + 1)
     opm_skew_adjoint(plan, x, r)
     r.sub_(measured)
-    losses.append(0.5 * float(r.double().pow(2).sum()))
-    return x, losses
+    final = 0.5 * float(r.double().pow(2).sum())
+    save(max(done, iters))
+    return x, losses + [final]

@@ -328,6 +328,7 @@ class LiveViewServer:
         self.inflight: deque = deque()
         self.done: List[Request] = []
         self.rejected: List[Request] = []
+        self.cancelled: List[Request] = []
         self.peak_in_use = 0
         self.ticks = 0
         self.batch_sizes: List[int] = []
@@ -337,37 +338,54 @@ class LiveViewServer:
         with self._lock:
             self._arrivals.append(req)
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraws a request that has not been admitted yet (still queued
+        for memory): it is returned to the caller's ring and listed in
+        ``cancelled``.  Admitted requests run to completion; returns False
+        for those and for unknown ids."""
+        with self._lock:
+            for q in (self._arrivals, self.waiting):
+                for req in q:
+                    if req.rid == rid:
+                        q.remove(req)
+                        req.error = "cancelled"
+                        req.t_done = time.perf_counter()
+                        req.release_host()
+                        self.cancelled.append(req)
+                        return True
+        return False
+
     # scheduler ----------------------------------------------------------
     def _admit(self) -> None:
         torch = self.torch
-        with self._lock:
+        with self._lock:                       # cancel() touches the same queues
             while self._arrivals:
                 self.waiting.append(self._arrivals.popleft())
-        while self.waiting:
-            req = self.waiting[0]
-            plan = self.plans.get(req.nscan, req.nrows, req.ncols)
-            need = request_bytes(plan, req.channels)
-            if need > self.arena.budget or result_bytes(plan, req.channels) > self.results.budget:
-                # can never fit: refuse, keep serving others
+            while self.waiting:
+                req = self.waiting[0]
+                plan = self.plans.get(req.nscan, req.nrows, req.ncols)
+                need = request_bytes(plan, req.channels)
+                if need > self.arena.budget or result_bytes(plan, req.channels) > self.results.budget:
+                    # can never fit: refuse, keep serving others
+                    self.waiting.popleft()
+                    req.error = (f"needs {need} device bytes (budget {self.arena.budget}) and "
+                                 f"{result_bytes(plan, req.channels)} result bytes ({self.results.budget})")
+                    req.t_done = time.perf_counter()
+                    self.rejected.append(req)
+                    req.release_host()
+                    continue
+                off = self.arena.alloc(need)
+                if off is None:                # wait for memory (FIFO, no overtaking)
+                    break
                 self.waiting.popleft()
-                req.error = (f"needs {need} device bytes (budget {self.arena.budget}) and "
-                             f"{result_bytes(plan, req.channels)} result bytes ({self.results.budget})")
-                req.t_done = time.perf_counter()
-                self.rejected.append(req)
-                req.release_host()
-                continue
-            off = self.arena.alloc(need)
-            if off is None:                    # wait for memory (FIFO, no overtaking)
-                break
-            self.waiting.popleft()
-            r = _Resident(req, plan, off, self.arena, torch)
-            with torch.cuda.stream(self.h2d):
-                r.raw.view(torch.int16).copy_(req.host.view(torch.int16), non_blocking=True)
-                r.h2d = torch.cuda.Event()
-                r.h2d.record(self.h2d)
-            req.t_admit = time.perf_counter()
-            self.resident.append(r)
-            self.peak_in_use = max(self.peak_in_use, self.arena.in_use)
+                r = _Resident(req, plan, off, self.arena, torch)
+                with torch.cuda.stream(self.h2d):
+                    r.raw.view(torch.int16).copy_(req.host.view(torch.int16), non_blocking=True)
+                    r.h2d = torch.cuda.Event()
+                    r.h2d.record(self.h2d)
+                req.t_admit = time.perf_counter()
+                self.resident.append(r)
+                self.peak_in_use = max(self.peak_in_use, self.arena.in_use)
 
     def _launch_tick(self) -> bool:
         torch = self.torch
@@ -444,17 +462,24 @@ class LiveViewServer:
         return True
 
     def step(self) -> None:
-        """One scheduler pass: admit, launch a tick, retire finished ticks."""
+        """One scheduler pass: admit, launch a tick, retire finished ticks
+        (each phase an NVTX range for timeline profilers)."""
+        nvtx = self.torch.cuda.nvtx
+        nvtx.range_push("opm.admit")
         self._admit()
+        nvtx.range_pop()
+        nvtx.range_push("opm.launch_tick")
         launched = self._launch_tick()
+        nvtx.range_pop()
         retired = self._retire(block=False)
         if not launched and not retired and self.inflight:
             # nothing else to do: wait for the oldest tick (frees memory too)
             self._retire(block=True)
 
     def run(self, n_expected: int, timeout_s: float = 600.0, idle=None) -> None:
+        """Serves until ``n_expected`` requests are done, rejected or cancelled."""
         t_end = time.perf_counter() + timeout_s
-        while len(self.done) + len(self.rejected) < n_expected:
+        while len(self.done) + len(self.rejected) + len(self.cancelled) < n_expected:
             if time.perf_counter() > t_end:
                 raise TimeoutError(f"served {len(self.done)} of {n_expected} requests")
             self.step()
@@ -518,8 +543,9 @@ class PlainServer:
         self.done.append(req)
 
     def run(self, n_expected: int, timeout_s: float = 600.0, idle=None) -> None:
+        """Serves until ``n_expected`` requests are done, rejected or cancelled."""
         t_end = time.perf_counter() + timeout_s
-        while len(self.done) + len(self.rejected) < n_expected:
+        while len(self.done) + len(self.rejected) + len(self.cancelled) < n_expected:
             if time.perf_counter() > t_end:
                 raise TimeoutError(f"served {len(self.done)} of {n_expected} requests")
             with self._lock:

@@ -121,3 +121,21 @@ def test_gradient_descent_reconstruction(lib, ag):
     err0 = float(gt.norm())
     err = float((x - gt).norm())
     assert err < 0.8 * err0
+
+
+def test_reconstruction_checkpoint_resume(lib, ag, tmp_path):
+    """An interrupted run resumed from its checkpoint ends on exactly the
+    iterate (and losses) of an uninterrupted run."""
+    plan = lib.Plan(32, 40, 48, 30.0, 0.4, 0.115)
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    measured = torch.rand(plan.raw_shape, generator=gen, device="cuda") * 100
+    L = ag.power_iteration(plan, iters=10)
+    x_full, l_full = ag.reconstruct(plan, measured, iters=25, eta=1.0 / L, lipschitz=L)
+    ck = str(tmp_path / "gd.pt")
+    ag.reconstruct(plan, measured, iters=20, eta=1.0 / L, lipschitz=L, checkpoint=ck, every=10)   # "interrupted"
+    x_res, l_res = ag.reconstruct(plan, measured, iters=25, checkpoint=ck, every=10)                # resumed
+    torch.cuda.synchronize()
+    assert torch.equal(x_res, x_full)
+    assert l_res == l_full
+    state = torch.load(ck)
+    assert state["iters"] == 25 and len(state["losses"]) == 25

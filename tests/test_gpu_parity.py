@@ -405,3 +405,83 @@ def test_deskew_dual_small(lib, shape, dtype):
     assert_close(f.cpu().numpy(), ref, what="dual f32")
     got = u.view(torch.int16).cpu().numpy().view(np.uint16).astype(np.int64)
     assert np.max(np.abs(got - O.to_u16(ref).astype(np.int64))) <= 1
+
+
+TINY = [(2, 1, 1, 90.0, 0.1, 0.1), (2, 1, 9, 45.0, 0.2, 0.115), (3, 2, 5, 30.0, 0.4, 0.115),
+        (2, 3, 7, 60.0, 0.1, 0.1), (4, 1, 3, 35.0, 0.05, 0.1), (5, 2, 2, 89.0, 0.3, 0.1)]
+
+
+@pytest.mark.parametrize("shape", TINY)
+def test_tiny_odd_shapes_every_kernel(lib, shape):
+    """Two planes, one row, 1..9 columns, 90 degrees: every call against the
+    oracle (degenerate extents and ragged vectors everywhere)."""
+    g = O.geometry(*shape)
+    R = (np.arange(np.prod(g.nscan * g.nrows * g.ncols)).reshape(g.nscan, g.nrows, g.ncols) * 37 % 1000 + 1
+         ).astype(np.uint16)
+    plan = lib.Plan(*shape)
+    raw = to_dev(R, torch)
+    Rf = R.astype(np.float64)
+    V = O.deskew(Rf, g)
+    assert_close(lib.deskew(plan, raw).cpu().numpy(), V, what="tiny deskew")
+    out = lib.project(plan, raw, zmip=True, zsum=True, ymip=True, argz=True)
+    zmip, zsum, ymip, _ = O.project(Rf, g)
+    assert_close(out["zmip"].cpu().numpy(), zmip, what="tiny zmip")
+    assert_close(out["zsum"].cpu().numpy(), zsum, what="tiny zsum")
+    assert_close(out["ymip"].cpu().numpy(), ymip, what="tiny ymip")
+    f = lib.project(plan, raw, zmip=True, ymip=True)
+    assert torch.equal(f["zmip"], out["zmip"]) and torch.equal(f["ymip"], out["ymip"])
+    vf = torch.empty(plan.vol_shape, device="cuda")
+    zm = torch.empty((plan.ny, plan.nx), device="cuda")
+    ym = torch.empty((plan.nz, plan.nx), device="cuda")
+    lib.opm_deskew_mip(plan, raw, vf, None, zm, ym)
+    zs, ys = torch.empty_like(zm), torch.empty_like(ym)
+    lib.opm_stream_begin(plan, zs, None, ys)
+    for n in range(-1, g.nscan):
+        lib.opm_stream_pair(plan, raw[n] if n >= 0 else None, raw[n + 1] if n + 1 < g.nscan else None, n, zs, None, ys)
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    assert torch.equal(vf, lib.deskew(plan, raw))
+    assert torch.equal(zm, f["zmip"]) and torch.equal(ym, f["ymip"])
+    assert torch.equal(zs, f["zmip"]) and torch.equal(ys, f["ymip"])
+    Y = opm_synth.gaussian(plan.vol_shape, 5, np.float32)
+    G = lib.skew_adjoint(plan, to_dev(Y, torch))
+    torch.cuda.synchronize()
+    assert_close(G.cpu().numpy(), O.skew_adjoint(Y.astype(np.float64), g), what="tiny adjoint")
+
+
+def test_one_plan_many_threads(lib):
+    """A plan is immutable after creation: several host threads use it on
+    their own streams at once and each gets the single-threaded result."""
+    import threading
+    shape = (64, 128, 128, 30.0, 0.4, 0.115)
+    plan = lib.Plan(*shape)
+    stacks = [to_dev(_stack(shape, seed=50 + i), torch) for i in range(4)]
+    ref = [lib.project(plan, r, zmip=True, ymip=True) for r in stacks]
+    vref = [lib.deskew(plan, r) for r in stacks]
+    torch.cuda.synchronize()
+    got = [None] * 4
+    errors = []
+
+    def work(i):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for _ in range(5):
+                    o = lib.project(plan, stacks[i], zmip=True, ymip=True, stream=s)
+                    v = lib.deskew(plan, stacks[i], stream=s)
+            s.synchronize()
+            got[i] = (o, v)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors
+    lib.opm_plan_check(plan)
+    for i in range(4):
+        o, v = got[i]
+        assert torch.equal(o["zmip"], ref[i]["zmip"]) and torch.equal(o["ymip"], ref[i]["ymip"])
+        assert torch.equal(v, vref[i])

@@ -97,7 +97,7 @@ def test_oversize_request_is_rejected_others_served(ring):
     srv.submit(huge)
     reqs = []
     for i, (n, r, c, C) in enumerate(SHAPES):
-        off = ring.acquire(2 * n * r * c * C)
+        off = ring.acquire(2 * n * r * c * C, timeout=5)
         reqs.append(Request(i, n, r, c, C, ring.view(off, (n, r, c * C)), ring=ring, ring_off=off))
         srv.submit(reqs[-1])
     srv.run(len(SHAPES) + 1, timeout_s=60)
@@ -122,3 +122,26 @@ def test_results_released_back_to_the_arena(ring):
     torch.cuda.synchronize()
     assert len(srv.done) == 30 and srv.results.in_use == 0
     assert all(r.results is None for r in srv.done)
+
+
+def test_cancel_queued_request(ring):
+    """A request still waiting for memory can be withdrawn; the others are
+    served and its ring range is returned."""
+    from paper_2211_00645_gb300.serve import LiveViewServer, PlanCache, Request, request_bytes
+    pc = PlanCache(*GEOM)
+    big = max(request_bytes(pc.get(n, r, c), C) for (n, r, c, C) in SHAPES)
+    srv = LiveViewServer(pc, big + 4096, max_items=16, max_units=1 << 16, result_bytes=64 << 20)
+    reqs = []
+    for i, (n, r, c, C) in enumerate(SHAPES + SHAPES[:2]):      # about 55 MB: fits the 64 MB ring
+        off = ring.acquire(2 * n * r * c * C, timeout=5)
+        reqs.append(Request(i, n, r, c, C, ring.view(off, (n, r, c * C)), ring=ring, ring_off=off))
+        srv.submit(reqs[-1])
+    srv._admit()                      # the budget holds about one request: the rest queue
+    assert srv.waiting, "expected queued requests"
+    victim = srv.waiting[-1].rid
+    assert srv.cancel(victim) and not srv.cancel(victim) and not srv.cancel(12345)
+    srv.run(len(reqs), timeout_s=60)
+    torch.cuda.synchronize()
+    assert [r.rid for r in srv.cancelled] == [victim]
+    assert len(srv.done) == len(reqs) - 1 and ring.in_use() == 0
+    _check_results(srv.done)

@@ -49,13 +49,13 @@ KERNEL_SOURCES = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per full-size
 # launch from ncu captures, keyed by the hash of the kernel's sources at
 # capture time (reported as null once a source has changed).  liveview:
-# captured at full size (200 x 512 x 2048): 451.05 MB read + 7.84 MB written.
-# volume_f32: captured with 100 scan planes (212.38 MB read, 2963.47 MB
+# captured at full size (200 x 512 x 2048): 450.97 MB read + 7.79 MB written.
+# volume_f32: captured with 100 scan planes (212.18 MB read, 2963.04 MB
 # written) and scaled to 200 planes, reads by the raw bytes (x2.0) and writes
 # by the volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "liveview": {"src_sha": "43a3ec7ec6b4", "bytes_per_launch": 458893312},
-    "volume_f32": {"src_sha": "70fa4038faa2", "bytes_per_launch": 4621287526},
+    "liveview": {"src_sha": "7e772d5d56c5", "bytes_per_launch": 458759424},
+    "volume_f32": {"src_sha": "439523dea4f0", "bytes_per_launch": 4620285304},
 }
 
 

@@ -7,6 +7,7 @@ paper_2211_00645_gb300.profile_case ...``).
   --kernel batch     batched live view over a mix of serving-sized stacks
   --kernel fused     volume + z-MIP + y-MIP in one pass (opm_deskew_mip)
   --kernel sheet     the sheet-frame view with the shear of Eq. 1 (opm_sheet_project)
+  --kernel pair      one plane-pair update of the plane-by-plane view (opm_stream_pair)
   --kernel batch1    the named stack alone through the persistent batch kernel
                      (--kchunk, --ctas: its launch shape)
   --nscan N          override the stack's scan-plane count (smaller captures)
@@ -32,7 +33,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["project", "deskew", "fused", "sheet", "batch", "batch1"], required=True)
+    ap.add_argument("--kernel", choices=["project", "deskew", "fused", "sheet", "pair", "batch", "batch1"], required=True)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--config", default="liveview_200x512x2048")
@@ -84,6 +85,13 @@ def main(argv=None):
 
             def launch():
                 b.launch(args.ctas, s)
+        elif args.kernel == "pair":
+            zmip = torch.zeros((plan.ny, plan.nx), device="cuda")
+            ymip = torch.zeros((plan.nz, plan.nx), device="cuda")
+            mid = cfg.nscan // 2
+
+            def launch():
+                opm.opm_stream_pair(plan, raw[mid], raw[mid + 1], mid, zmip, None, ymip, s)
         elif args.kernel == "sheet":
             import math
             shear = cfg.step * math.cos(math.radians(cfg.theta_deg)) / cfg.pixel

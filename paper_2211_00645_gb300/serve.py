@@ -505,6 +505,7 @@ class PlainServer:
         self._arrivals: deque = deque()
         self.done: List[Request] = []
         self.rejected: List[Request] = []
+        self.cancelled: List[Request] = []   # kept for the common run() contract; the plain path has no queue
 
     def submit(self, req: Request) -> None:
         with self._lock:

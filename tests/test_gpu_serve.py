@@ -145,3 +145,16 @@ def test_cancel_queued_request(ring):
     assert [r.rid for r in srv.cancelled] == [victim]
     assert len(srv.done) == len(reqs) - 1 and ring.in_use() == 0
     _check_results(srv.done)
+
+
+def test_plain_server_run_loop(ring):
+    """The plain path's own run loop with a camera: every request served,
+    results equal to the batched server's on the same bytes."""
+    from paper_2211_00645_gb300.serve import Camera, PlainServer, PlanCache
+    srv = PlainServer(PlanCache(*GEOM), result_bytes=64 << 20)
+    cam = Camera(srv, ring, SHAPES, 12, 500.0, seed=8)
+    cam.start()
+    srv.run(cam.expected(), timeout_s=120)
+    cam.join(timeout=30)
+    assert cam.error is None and len(srv.done) == 12 and ring.in_use() == 0
+    _check_results(srv.done)

@@ -205,6 +205,7 @@ class Request:
     t_launch: float = 0.0    # projection launched
     res_arena: Optional["DeviceArena"] = None  # pinned arena holding ``results``
     res_off: int = -1
+    geometry: Optional[Tuple[float, float, float]] = None  # (theta, step, pixel) it was served with
 
     def release_host(self) -> None:
         if self.ring is not None:
@@ -275,6 +276,30 @@ class PlanCache:
             self._plans[key] = Plan(*key, self.theta_deg, self.step, self.pixel)
         return self._plans[key]
 
+    @property
+    def geometry(self) -> Tuple[float, float, float]:
+        return (self.theta_deg, self.step, self.pixel)
+
+
+class _Geometries:
+    """The servers' current plan cache, switchable while serving (the paper
+    lets the user change the deskew parameters during imaging).  Caches of
+    earlier geometries are kept, so switching back re-creates no plan."""
+
+    def __init__(self, plans: PlanCache):
+        self.current = plans
+        self._all = {plans.geometry: plans}
+
+    def cache(self, theta_deg: float, step: float, pixel: float) -> PlanCache:
+        key = (float(theta_deg), float(step), float(pixel))
+        if key not in self._all:
+            self._all[key] = PlanCache(*key)
+        return self._all[key]
+
+    def set(self, theta_deg: float, step: float, pixel: float) -> PlanCache:
+        self.current = self.cache(theta_deg, step, pixel)
+        return self.current
+
 
 class _Resident:
     """A request admitted to the device: arena range, device views, events."""
@@ -308,7 +333,7 @@ class LiveViewServer:
 
         from . import Batch
         self.torch = torch
-        self.plans = plans
+        self._geo = _Geometries(plans)
         self.arena = DeviceArena(budget_bytes, base=torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda"))
         # pinned destination of the read-back, allocated once
         self.results = DeviceArena(result_bytes, base=torch.empty(int(result_bytes), dtype=torch.uint8,
@@ -332,6 +357,16 @@ class LiveViewServer:
         self.peak_in_use = 0
         self.ticks = 0
         self.batch_sizes: List[int] = []
+
+    @property
+    def plans(self) -> PlanCache:
+        return self._geo.current
+
+    def set_geometry(self, theta_deg: float, step: float, pixel: float) -> None:
+        """New deskew parameters for requests admitted from now on; those
+        already admitted finish with theirs.  Batches may mix geometries."""
+        with self._lock:
+            self._geo.set(theta_deg, step, pixel)
 
     # producer side ------------------------------------------------------
     def submit(self, req: Request) -> None:
@@ -364,6 +399,7 @@ class LiveViewServer:
             while self.waiting:
                 req = self.waiting[0]
                 plan = self.plans.get(req.nscan, req.nrows, req.ncols)
+                req.geometry = self.plans.geometry
                 need = request_bytes(plan, req.channels)
                 if need > self.arena.budget or result_bytes(plan, req.channels) > self.results.budget:
                     # can never fit: refuse, keep serving others
@@ -497,7 +533,7 @@ class PlainServer:
     def __init__(self, plans: PlanCache, keep_results: bool = True, result_bytes: int = 1 << 30):
         import torch
         self.torch = torch
-        self.plans = plans
+        self._geo = _Geometries(plans)
         self.keep_results = keep_results
         self.results = DeviceArena(result_bytes, base=torch.empty(int(result_bytes), dtype=torch.uint8,
                                                                   pin_memory=True))
@@ -507,6 +543,14 @@ class PlainServer:
         self.rejected: List[Request] = []
         self.cancelled: List[Request] = []   # kept for the common run() contract; the plain path has no queue
 
+    @property
+    def plans(self) -> PlanCache:
+        return self._geo.current
+
+    def set_geometry(self, theta_deg: float, step: float, pixel: float) -> None:
+        with self._lock:
+            self._geo.set(theta_deg, step, pixel)
+
     def submit(self, req: Request) -> None:
         with self._lock:
             self._arrivals.append(req)
@@ -514,7 +558,10 @@ class PlainServer:
     def _serve(self, req: Request) -> None:
         from . import opm_project
         torch = self.torch
-        plan = self.plans.get(req.nscan, req.nrows, req.ncols)
+        # a request that names its geometry is served with it, else the current one
+        plans = self.plans if req.geometry is None else self._geo.cache(*req.geometry)
+        plan = plans.get(req.nscan, req.nrows, req.ncols)
+        req.geometry = plans.geometry
         off = self.results.alloc(result_bytes(plan, req.channels))
         if off is None:
             req.error = "result buffers exhausted (keep_results without release_results)"

@@ -26,9 +26,10 @@ def _check_results(reqs):
     plain = PlainServer(PlanCache(*GEOM), result_bytes=64 << 20)
     ref = {}
     for req in reqs:
-        key = (req.host.data_ptr(), tuple(req.host.shape), req.channels)
+        key = (req.host.data_ptr(), tuple(req.host.shape), req.channels, req.geometry)
         if key not in ref:
-            plain._serve(Request(req.rid, req.nscan, req.nrows, req.ncols, req.channels, req.host))
+            plain._serve(Request(req.rid, req.nscan, req.nrows, req.ncols, req.channels, req.host,
+                                 geometry=req.geometry))
             ref[key] = plain.done[-1].results
         want = ref[key]
         assert len(req.results) == len(want) == req.channels
@@ -157,4 +158,33 @@ def test_plain_server_run_loop(ring):
     srv.run(cam.expected(), timeout_s=120)
     cam.join(timeout=30)
     assert cam.error is None and len(srv.done) == 12 and ring.in_use() == 0
+    _check_results(srv.done)
+
+
+def test_geometry_change_while_serving(ring):
+    """New deskew parameters mid-stream: requests admitted before keep
+    theirs, later ones use the new plans (batches may mix both), and every
+    result equals the plain path with the geometry it was served with."""
+    from paper_2211_00645_gb300.serve import LiveViewServer, PlanCache, Request
+    srv = LiveViewServer(PlanCache(*GEOM), 256 << 20, max_items=16, max_units=1 << 16, result_bytes=64 << 20)
+    reqs = []
+
+    def submit(i, shape):
+        n, r, c, C = shape
+        off = ring.acquire(2 * n * r * c * C, timeout=5)
+        reqs.append(Request(i, n, r, c, C, ring.view(off, (n, r, c * C)), ring=ring, ring_off=off))
+        srv.submit(reqs[-1])
+
+    for i, shp in enumerate(SHAPES):
+        submit(i, shp)
+    srv.step()                                    # admits (and may launch) the first five
+    srv.set_geometry(45.0, 0.2, 0.115)
+    for i, shp in enumerate(SHAPES):
+        submit(10 + i, shp)
+    srv.run(len(reqs), timeout_s=60)
+    torch.cuda.synchronize()
+    assert len(srv.done) == len(reqs) and ring.in_use() == 0
+    geos = {r.rid: r.geometry for r in srv.done}
+    assert all(geos[i] == GEOM for i in range(5))
+    assert all(geos[10 + i] == (45.0, 0.2, 0.115) for i in range(5))
     _check_results(srv.done)

@@ -8,6 +8,13 @@ each new frame n is copied in and the voxels whose lower plane is n - 1 are
 folded into the projections (``opm_stream_pair``); the frame after the last
 closes the stack.  In rolling mode every push returns the projections so
 far; in global mode only the push that completes a stack does.
+
+A third mode, sliding, keeps the latest frame of every scan position in a
+device stack buffer (frame n of the current stack replaces frame n of the
+previous one) and re-projects the whole buffer after every frame with the
+fused projection, so the view always spans a full stack: the newest frames
+where they exist, the previous stack's elsewhere (zeros before the first
+stack completes).
 """
 from __future__ import annotations
 
@@ -22,13 +29,17 @@ class RollingView:
 
     def __init__(self, plan: Plan, mode: str = "rolling", zsum: bool = False, stream=None):
         import torch
-        if mode not in ("rolling", "global"):
-            raise ValueError("mode must be 'rolling' or 'global'")
+        if mode not in ("rolling", "global", "sliding"):
+            raise ValueError("mode must be 'rolling', 'global' or 'sliding'")
         self.torch = torch
         self.plan, self.mode = plan, mode
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         dev = torch.device("cuda", torch.cuda.current_device())
-        self.frames = [torch.empty((plan.nrows, plan.ncols), dtype=torch.uint16, device=dev) for _ in range(2)]
+        if mode == "sliding":
+            self.stack = torch.zeros(plan.raw_shape, dtype=torch.int16, device=dev).view(torch.uint16)
+            self.frames = []
+        else:
+            self.frames = [torch.empty((plan.nrows, plan.ncols), dtype=torch.uint16, device=dev) for _ in range(2)]
         self.zmip = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
         self.ymip = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
         self.zsum = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev) if zsum else None
@@ -46,6 +57,8 @@ class RollingView:
         p = self.plan
         if tuple(frame.shape) != (p.nrows, p.ncols) or frame.dtype != torch.uint16:
             raise ValueError(f"frame must be uint16 {(p.nrows, p.ncols)}")
+        if self.mode == "sliding":
+            return self._push_sliding(frame)
         cur = self.frames[self.n % 2]
         with torch.cuda.stream(self.stream):
             cur.view(torch.int16).copy_(frame.view(torch.int16), non_blocking=True)
@@ -67,3 +80,21 @@ class RollingView:
                 out["zsum"] = zsum
             return out
         return None
+
+    def _push_sliding(self, frame) -> dict:
+        from . import opm_project
+        torch = self.torch
+        p = self.plan
+        with torch.cuda.stream(self.stream):
+            self.stack[self.n].view(torch.int16).copy_(frame.view(torch.int16), non_blocking=True)
+        opm_project(p, self.stack, self.zmip, self.zsum, self.ymip, None, self.stream)
+        self.n += 1
+        complete = self.n == p.nscan
+        if complete:
+            self.n = 0
+            self.stacks += 1
+        out = {"zmip": self.zmip, "ymip": self.ymip, "frames": p.nscan if complete else self.n,
+               "complete": complete, "stacks": self.stacks}
+        if self.zsum is not None:
+            out["zsum"] = self.zsum
+        return out

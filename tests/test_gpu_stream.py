@@ -123,3 +123,31 @@ def test_stream_argument_checks(lib):
         assert e.value.status == lib.OPM_ERR_INVALID_ARG
     with pytest.raises(lib.OpmError):
         lib.opm_stream_begin(plan, None, None, None)
+
+
+def test_sliding_mode_spans_a_full_stack(lib):
+    """Sliding mode: after frames 0..m-1 of the second stack, the view is the
+    projection of (second stack's frames 0..m-1, first stack's m..N-1)."""
+    from paper_2211_00645_gb300.rolling import RollingView
+    shape = SHAPES[2]
+    plan = lib.Plan(*shape)
+    A, B = _stack(shape, seed=21), _stack(shape, seed=22)
+    view = RollingView(plan, mode="sliding")
+    ha = torch.from_numpy(A.view(np.int16)).view(torch.uint16)
+    hb = torch.from_numpy(B.view(np.int16)).view(torch.uint16)
+    for n in range(plan.nscan):
+        out = view.push(ha[n])
+    assert out["complete"] and out["stacks"] == 1
+    torch.cuda.synchronize()
+    full_a = lib.project(plan, to_dev(A, torch), zmip=True, ymip=True)
+    assert torch.equal(out["zmip"], full_a["zmip"]) and torch.equal(out["ymip"], full_a["ymip"])
+    m = 17
+    for n in range(m):
+        out = view.push(hb[n])
+    torch.cuda.synchronize()
+    mixed = np.concatenate([B[:m], A[m:]], axis=0)
+    ref = lib.project(plan, to_dev(mixed, torch), zmip=True, ymip=True)
+    assert out["frames"] == m and not out["complete"]
+    assert torch.equal(out["zmip"], ref["zmip"]) and torch.equal(out["ymip"], ref["ymip"])
+    zr, _, yr, _ = O.project(mixed.astype(np.float64), O.geometry(*shape))
+    assert_close(out["zmip"].cpu().numpy(), zr, what="sliding zmip")

@@ -12,8 +12,8 @@ namespace opm {
 namespace {
 
 constexpr int kThreadsX = 32;  // lanes along x
-constexpr int kThreadsY = 8;   // j-runs per CTA
-constexpr int kRunJ = 8;       // output columns per thread
+constexpr int kThreadsY = 4;   // j-runs per CTA
+constexpr int kRunJ = 32;      // output columns per thread
 
 template <typename T, int N, typename Acc>
 __device__ __forceinline__ void load_half(const T* __restrict__ p, bool vec, int lim, Acc (&out)[N]) {
@@ -170,20 +170,21 @@ opm_status run(const opm_plan* p, const void* raw, void* vol, void* vol2, cudaSt
 // combines are maxima of non-negative values on their bit patterns, so the
 // result does not depend on their order.
 constexpr int kMipRows = 64;
+constexpr int kMipWarps = 8;  // warps (runs of kMipJ columns) per CTA
 constexpr int kMipJ = 4;     // columns j per thread
 constexpr int kMipVec = 4;   // columns x per lane
 
 template <bool F32, bool U16>
-__global__ void __launch_bounds__(kThreadsX* kThreadsY, 4)
+__global__ void __launch_bounds__(kThreadsX* kMipWarps, 4)
 k_deskew_mip(PlanView v, const uint16_t* __restrict__ raw, float* __restrict__ volf, uint16_t* __restrict__ volh,
              float* __restrict__ zmip, float* __restrict__ ymip, int in_vec_ok, int out_vec_ok) {
   __shared__ float ybuf[kMipRows][kThreadsX * kMipVec];
   const int lane = threadIdx.x, w = threadIdx.y;
   const int x = blockIdx.x * kThreadsX * kMipVec + lane * kMipVec;
-  const int jb = (blockIdx.y * kThreadsY + w) * kMipJ;
+  const int jb = (blockIdx.y * kMipWarps + w) * kMipJ;
   const int k0 = blockIdx.z * kMipRows;
   const int k1 = min(k0 + kMipRows, v.nz);
-  for (int i = threadIdx.y * kThreadsX + threadIdx.x; i < kMipRows * kThreadsX * kMipVec; i += kThreadsX * kThreadsY)
+  for (int i = threadIdx.y * kThreadsX + threadIdx.x; i < kMipRows * kThreadsX * kMipVec; i += kThreadsX * kMipWarps)
     (&ybuf[0][0])[i] = 0.0f;
   __syncthreads();
   const bool active = x < v.nx && jb < v.ny;
@@ -287,7 +288,7 @@ k_deskew_mip(PlanView v, const uint16_t* __restrict__ raw, float* __restrict__ v
     __syncthreads();
     const int xb = blockIdx.x * kThreadsX * kMipVec;
     for (int i = threadIdx.y * kThreadsX + threadIdx.x; i < (k1 - k0) * kThreadsX * kMipVec;
-         i += kThreadsX * kThreadsY) {
+         i += kThreadsX * kMipWarps) {
       const int kk = i / (kThreadsX * kMipVec), xx = i % (kThreadsX * kMipVec);
       if (xb + xx < v.nx)
         atomicMax(reinterpret_cast<int*>(ymip + (size_t)(k0 + kk) * v.nx + xb + xx), __float_as_int(ybuf[kk][xx]));
@@ -340,7 +341,7 @@ opm_status launch_deskew_mip(const opm_plan* p, const void* raw, opm_dtype in_t,
     return launch_project(p, raw, in_t, zmip, nullptr, ymip, nullptr, s);
   }
   const int xtiles = (v.nx + kThreadsX * kMipVec - 1) / (kThreadsX * kMipVec);
-  const int jblocks = (v.ny + kThreadsY * kMipJ - 1) / (kThreadsY * kMipJ);
+  const int jblocks = (v.ny + kMipWarps * kMipJ - 1) / (kMipWarps * kMipJ);
   const int kchunks = (v.nz + kMipRows - 1) / kMipRows;
   if (jblocks > 65535 || kchunks > 65535) return fail(OPM_ERR_UNSUPPORTED, "deskew grid exceeds launch limits");
   if (zmip || ymip) {
@@ -350,7 +351,7 @@ opm_status launch_deskew_mip(const opm_plan* p, const void* raw, opm_dtype in_t,
   }
   const int in_vec_ok = (v.ncols % kMipVec == 0) && ((uintptr_t)raw % 8 == 0);
   const int out_vec_ok = (v.nx % kMipVec == 0) && ((uintptr_t)volf % 16 == 0) && ((uintptr_t)volh % 8 == 0);
-  dim3 grid(xtiles, jblocks, kchunks), block(kThreadsX, kThreadsY);
+  dim3 grid(xtiles, jblocks, kchunks), block(kThreadsX, kMipWarps);
   const uint16_t* r = static_cast<const uint16_t*>(raw);
   if (volf && volh)
     k_deskew_mip<true, true><<<grid, block, 0, s>>>(v, r, volf, volh, zmip, ymip, in_vec_ok, out_vec_ok);

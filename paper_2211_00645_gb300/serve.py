@@ -354,6 +354,8 @@ class LiveViewServer:
         self.done: List[Request] = []
         self.rejected: List[Request] = []
         self.cancelled: List[Request] = []
+        self.poll_s = 50e-6     # scheduler poll interval while the device is busy
+        self.host_set_s = 0.0   # host time spent building work lists
         self.peak_in_use = 0
         self.ticks = 0
         self.batch_sizes: List[int] = []
@@ -453,7 +455,9 @@ class LiveViewServer:
             for c in range(C):
                 items.append({"plan": r.plan, "raw": r.raw[:, :, c * n:], "row_pitch": C * n,
                               "plane_pitch": r.plan.nrows * C * n, "zmip": r.z[c], "ymip": r.y[c]})
+        t_set = time.perf_counter()
         b.set(items, self.kchunk)
+        self.host_set_s += time.perf_counter() - t_set
         for r in ready:
             self.comp.wait_event(r.h2d)
             r.launched = True
@@ -509,8 +513,16 @@ class LiveViewServer:
         nvtx.range_pop()
         retired = self._retire(block=False)
         if not launched and not retired and self.inflight:
-            # nothing else to do: wait for the oldest tick (frees memory too)
-            self._retire(block=True)
+            # nothing to launch or retire yet: hand landed copies' ring ranges
+            # back to the camera and poll again shortly (a blocking wait on
+            # the oldest tick would hold them and stall the camera)
+            self._release_landed()
+            time.sleep(self.poll_s)
+
+    def _release_landed(self) -> None:
+        for r in self.resident:
+            if not r.launched and r.req.ring is not None and r.h2d.query():
+                r.req.release_host()
 
     def run(self, n_expected: int, timeout_s: float = 600.0, idle=None) -> None:
         """Serves until ``n_expected`` requests are done, rejected or cancelled."""
@@ -683,5 +695,8 @@ def serve_stats(server, t_first: float) -> dict:
     for k, v in parts.items():
         out[f"{k}_p50_ms"] = percentile(v, 50)
         out[f"{k}_p99_ms"] = percentile(v, 99)
+    if getattr(server, "ticks", 0):
+        out["ticks"] = server.ticks
+        out["host_set_ms_per_tick"] = server.host_set_s * 1e3 / server.ticks
     return out
 

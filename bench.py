@@ -257,6 +257,42 @@ def tune_serving(torch, plans, ring):
     return e
 
 
+def adjoint_bench(torch, opm, peak):
+    """Forward deskew, skew adjoint and z-MIP backward (FP32) on the
+    differentiable workload 128 x 256 x 256 (theta 30, step 0.4, pixel
+    0.115), each timed with CUDA events against its algorithmic bytes."""
+    c = opm_synth.CONFIGS["diff_128x256x256"]
+    p = opm.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    s = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(p.raw_shape, generator=g, device="cuda")
+    v = torch.empty(p.vol_shape, device="cuda")
+    r = torch.empty(p.raw_shape, device="cuda")
+    gz = torch.randn((p.ny, p.nx), generator=g, device="cuda")
+    argz = torch.randint(0, p.nz, (p.ny, p.nx), generator=g, device="cuda", dtype=torch.int32)
+    raw_b, vol_b = 4 * x.numel(), 4 * v.numel()
+    calls = {
+        "forward_f32": (lambda: opm.opm_deskew(p, x, v, s), raw_b + vol_b),
+        "skew_adjoint_f32": (lambda: opm.opm_skew_adjoint(p, v, r, s), vol_b + raw_b),
+        "mip_backward": (lambda: opm.opm_mip_backward(p, gz, argz, r, s), 8 * gz.numel() + raw_b),
+    }
+    out = {"workload": "diff_128x256x256", "grid": [p.nz, p.ny, p.nx]}
+    for name, (fn, nbytes) in calls.items():
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(50):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 50 * 1e-3
+        out[name] = {"bytes": nbytes, "us": round(t * 1e6, 2), "GBps": round(nbytes / t / 1e9, 1),
+                     "frac": round(nbytes / t / 1e9 / peak, 4)}
+    return out
+
+
 def rolling_bench(torch, opm, plan, host_raw, raw):
     """Frame-by-frame live view of the live-view stack (Fig. 4 rolling and
     global modes): every frame is copied in from pinned host memory and its
@@ -588,6 +624,7 @@ def main():
                           "out": list(sheet.shape), "bytes": sheet_b, "us": round(t_sheet * 1e6, 2),
                           "GBps": round(sheet_b / t_sheet / 1e9, 1), "frac": round(sheet_b / t_sheet / 1e9 / peak, 4)}
     del sheet
+    line["differentiable"] = adjoint_bench(torch, opm, peak)
     line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
     if args.serve_paced > 0 or args.serve_saturated > 0:
         del vol, raw

@@ -1,11 +1,13 @@
 // Adjoint of the deskew and backward pass of the z-MIP.
 //
-// Both are gathers over the transpose of the interpolation map: raw sample
-// (n, k, x) collects every output column j of row k whose lower plane n0(j,k)
-// is n (weight 1 - w) or n - 1 (weight w), in ascending j.  The weights are
+// Both apply the transpose of the interpolation map: raw sample (n, k, x)
+// collects every output column j of row k whose lower plane n0(j,k) is n
+// (weight 1 - w) or n - 1 (weight w), in ascending j.  The weights are
 // computed with the forward kernels' own split-table formula, so the adjoint
 // is the exact transpose of the map the forward kernels apply.  No atomics:
-// results are bitwise reproducible.
+// results are bitwise reproducible.  The adjoint gathers per raw sample; the
+// z-MIP backward, whose input is non-zero on one row per column, scatters.
+#include <algorithm>
 #include <cmath>
 
 #include "opm_common.cuh"
@@ -26,84 +28,176 @@ __device__ __forceinline__ void j_window(const PlanView& v, Split b, int n, int&
   jhi = min(v.ny - 1, (int)ceilf(hi) + 2);
 }
 
-template <typename T, typename Acc, int VEC, bool MIPBWD>
+// kPlanes consecutive planes n per thread share one walk over j; kUnroll
+// columns j have their loads issued together.
+template <typename T, typename Acc, int VEC, int kPlanes, int kUnroll>
 __global__ void __launch_bounds__(kThreadsX* kThreadsY)
-k_gather_t(PlanView v, const T* __restrict__ src, const int32_t* __restrict__ argz,
-           T* __restrict__ dst, int xtiles, int vec_ok) {
+k_gather_t(PlanView v, const T* __restrict__ src, T* __restrict__ dst, int xtiles, int vec_ok) {
   const int k = blockIdx.x / xtiles;
   const int xt = blockIdx.x - k * xtiles;
   const int x0 = (xt * kThreadsX + threadIdx.x) * VEC;
-  const int n = blockIdx.y * kThreadsY + threadIdx.y;
-  if (x0 >= v.nx || n >= v.nscan) return;
+  const int nb = (blockIdx.y * kThreadsY + threadIdx.y) * kPlanes;  // first plane of this thread
+  if (x0 >= v.nx || nb >= v.nscan) return;
   const int lim = v.nx - x0;
   const bool vec = vec_ok && lim >= VEC;
   const Split b = v.B[k];
-  int jlo, jhi;
-  j_window(v, b, n, jlo, jhi);
+  int jlo, jhi, dummy;
+  j_window(v, b, nb, jlo, dummy);
+  j_window(v, b, min(nb + kPlanes - 1, v.nscan - 1), dummy, jhi);
 
-  Acc acc[VEC];
+  Acc acc[kPlanes][VEC];
 #pragma unroll
-  for (int i = 0; i < VEC; ++i) acc[i] = Acc(0);
+  for (int q = 0; q < kPlanes; ++q)
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) acc[q][i] = Acc(0);
 
+  // plane nb + q takes (1 - w) from columns with n0 == nb + q and w from
+  // columns with n0 + 1 == nb + q, each plane in ascending j.  Columns are
+  // taken kUnroll at a time so that their loads are in flight together.
 #pragma unroll 1
-  for (int j = jlo; j <= jhi; ++j) {
-    int n0;
-    Acc w;
-    plane_weight_t<Acc>(v.A[j], b, v.linear, n0, w);
-    Acc wt;
-    if (n0 == n)
-      wt = Acc(1) - w;
-    else if (n0 + 1 == n)
-      wt = w;
-    else
-      continue;
-    if (wt == Acc(0)) continue;
-    Acc val[VEC];
-    if constexpr (MIPBWD) {
-      // g_zmip[j][x] where argz[j][x] == k, else 0
-      const size_t off = (size_t)j * v.nx + x0;
-      load_vec<T, VEC, Acc>(src + off, vec, lim, val);
-      if (vec) {
-        const int4 a4 = __ldg(reinterpret_cast<const int4*>(argz + off));
-        const int* ai = reinterpret_cast<const int*>(&a4);
+  for (int j0 = jlo; j0 <= jhi; j0 += kUnroll) {
+    Acc val[kUnroll][VEC], ws[kUnroll];
+    int q0s[kUnroll];
+    bool ul[kUnroll], uh[kUnroll];
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) val[i] = ai[i] == k ? val[i] : Acc(0);
-      } else {
-#pragma unroll
-        for (int i = 0; i < VEC; ++i) val[i] = (i < lim && __ldg(argz + off + i) == k) ? val[i] : Acc(0);
+    for (int u = 0; u < kUnroll; ++u) {
+      const int j = j0 + u;
+      ul[u] = uh[u] = false;
+      q0s[u] = 0;
+      ws[u] = Acc(0);
+      if (j <= jhi) {
+        int n0;
+        Acc w;
+        plane_weight_t<Acc>(v.A[j], b, v.linear, n0, w);
+        const int q0 = n0 - nb;  // plane index taking 1 - w; q0 + 1 takes w
+        q0s[u] = q0;
+        ws[u] = w;
+        ul[u] = q0 >= 0 && q0 < kPlanes && Acc(1) - w != Acc(0);
+        uh[u] = q0 + 1 >= 0 && q0 + 1 < kPlanes && w != Acc(0);
       }
-    } else {
-      load_vec<T, VEC, Acc>(src + ((size_t)k * v.ny + j) * v.nx + x0, vec, lim, val);
+      if (ul[u] || uh[u]) load_vec<T, VEC, Acc>(src + ((size_t)k * v.ny + j) * v.nx + x0, vec, lim, val[u]);
     }
 #pragma unroll
-    for (int i = 0; i < VEC; ++i) acc[i] = fma(wt, val[i], acc[i]);
+    for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+      for (int q = 0; q < kPlanes; ++q) {
+        if (ul[u] && q == q0s[u]) {
+          const Acc wl = Acc(1) - ws[u];
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) acc[q][i] = fma(wl, val[u][i], acc[q][i]);
+        }
+        if (uh[u] && q == q0s[u] + 1) {
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) acc[q][i] = fma(ws[u], val[u][i], acc[q][i]);
+        }
+      }
+    }
   }
 
-  T* op = dst + ((size_t)n * v.nrows + k) * v.ncols + x0;
-  if (vec) {
-    if constexpr (sizeof(T) == 4) {
-      *reinterpret_cast<float4*>(op) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+#pragma unroll
+  for (int q = 0; q < kPlanes; ++q) {
+    if (nb + q >= v.nscan) break;
+    T* op = dst + ((size_t)(nb + q) * v.nrows + k) * v.ncols + x0;
+    if (vec) {
+      if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(op) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+      } else {
+        *reinterpret_cast<double2*>(op) = make_double2(acc[q][0], acc[q][1]);
+      }
     } else {
-      *reinterpret_cast<double2*>(op) = make_double2(acc[0], acc[1]);
+      for (int i = 0; i < VEC && i < lim; ++i) op[i] = (T)acc[q][i];
     }
-  } else {
-    for (int i = 0; i < VEC && i < lim; ++i) op[i] = (T)acc[i];
   }
 }
 
-template <typename T, typename Acc, int VEC, bool MIPBWD>
-opm_status run(const opm_plan* p, const T* src, const int32_t* argz, T* dst, cudaStream_t s) {
+// ---------------------------------------------------------------- z-MIP backward
+//
+// The z-MIP gradient reaches the raw grid only through the arg-max row of
+// each (j, x): at most 2 ny nx of the nscan nrows ncols raw samples are
+// non-zero.  So the output is zero-filled at copy bandwidth and each (j, x)
+// then fills the one or two samples it feeds, (n0, k, x) with 1 - w and
+// (n0 + 1, k, x) with w, k = argz[j][x].  Several columns j of one x can
+// feed the same sample; its smallest such j (inside the sample's search
+// window) owns it and sums every feeding column in ascending j, the same
+// terms in the same order as the gather above, so the result is the same bit
+// for bit, without atomics.
+
+constexpr int kScX = 32;  // lanes along x (coalesced argz / g reads)
+constexpr int kScY = 8;   // columns j per CTA (one per warp)
+
+// Weight of column jj for raw plane n of row b (0 when it does not feed it).
+__device__ __forceinline__ float feed_weight(const PlanView& v, Split b, int jj, int n) {
+  int n0;
+  float w;
+  plane_weight(v.A[jj], b, v.linear, n0, w);
+  if (n0 == n) return 1.0f - w;
+  if (n0 + 1 == n) return w;
+  return 0.0f;
+}
+
+__global__ void __launch_bounds__(kScX* kScY)
+k_mip_scatter(PlanView v, const float* __restrict__ g, const int32_t* __restrict__ argz, float* __restrict__ g_raw) {
+  const int x = blockIdx.x * kScX + threadIdx.x;
+  const int j = blockIdx.y * kScY + threadIdx.y;
+  if (x >= v.nx || j >= v.ny) return;
+  const int k = __ldg(argz + (size_t)j * v.nx + x);
+  if (k < 0 || k >= v.nz) return;  // feeds no raw sample
+  const Split b = v.B[k];
+  int n0;
+  float w;
+  plane_weight(v.A[j], b, v.linear, n0, w);
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    const int n = n0 + t;
+    const float wj = t == 0 ? 1.0f - w : w;
+    if (n < 0 || n >= v.nscan || wj == 0.0f) continue;
+    int jlo, jhi;
+    j_window(v, b, n, jlo, jhi);
+    if (j < jlo || j > jhi) continue;
+    bool owner = true;
+#pragma unroll 1
+    for (int jj = jlo; jj < j; ++jj) {
+      if (__ldg(argz + (size_t)jj * v.nx + x) == k && feed_weight(v, b, jj, n) != 0.0f) {
+        owner = false;
+        break;
+      }
+    }
+    if (!owner) continue;
+    float acc = fmaf(wj, __ldg(g + (size_t)j * v.nx + x), 0.0f);
+#pragma unroll 1
+    for (int jj = j + 1; jj <= jhi; ++jj) {
+      if (__ldg(argz + (size_t)jj * v.nx + x) != k) continue;
+      const float wt = feed_weight(v, b, jj, n);
+      if (wt != 0.0f) acc = fmaf(wt, __ldg(g + (size_t)jj * v.nx + x), acc);
+    }
+    g_raw[((size_t)n * v.nrows + k) * v.ncols + x] = acc;
+  }
+}
+
+__global__ void k_fill_zero(float* __restrict__ p, long long n, int vec_ok) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec_ok) {
+    float4* q = reinterpret_cast<float4*>(p);
+    const long long n4 = n / 4;
+    for (; i < n4; i += stride) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  for (; i < n; i += stride) p[i] = 0.0f;
+}
+
+template <typename T, typename Acc, int VEC, int kPlanes, int kUnroll>
+opm_status run(const opm_plan* p, const T* src, T* dst, cudaStream_t s) {
   const PlanView& v = p->view;
   const int xtiles = (v.nx + kThreadsX * VEC - 1) / (kThreadsX * VEC);
   const long long gx = (long long)xtiles * v.nz;
-  const long long gy = (v.nscan + kThreadsY - 1) / kThreadsY;
+  const long long gy = (v.nscan + kThreadsY * kPlanes - 1) / (kThreadsY * kPlanes);
   if (gx > 0x7fffffffLL || gy > 65535)
     return fail(OPM_ERR_UNSUPPORTED, "adjoint grid exceeds launch limits");
-  int vec_ok = (v.nx % VEC == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
-  if (MIPBWD) vec_ok = vec_ok && ((uintptr_t)argz % 16 == 0);
+  const int vec_ok = (v.nx % VEC == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
   dim3 block(kThreadsX, kThreadsY);
   dim3 grid((unsigned)gx, (unsigned)gy);
-  k_gather_t<T, Acc, VEC, MIPBWD><<<grid, block, 0, s>>>(v, src, argz, dst, xtiles, vec_ok);
+  k_gather_t<T, Acc, VEC, kPlanes, kUnroll><<<grid, block, 0, s>>>(v, src, dst, xtiles, vec_ok);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch adjoint gather");
 }
@@ -113,17 +207,34 @@ opm_status run(const opm_plan* p, const T* src, const int32_t* argz, T* dst, cud
 opm_status launch_adjoint(const opm_plan* p, const void* vol, void* raw_out, opm_dtype t,
                           cudaStream_t s) {
   if (t == OPM_F32)
-    return run<float, float, 4, false>(p, static_cast<const float*>(vol), nullptr,
+    return run<float, float, 4, 2, 2>(p, static_cast<const float*>(vol),
                                        static_cast<float*>(raw_out), s);
   if (t == OPM_F64)
-    return run<double, double, 2, false>(p, static_cast<const double*>(vol), nullptr,
+    return run<double, double, 2, 1, 1>(p, static_cast<const double*>(vol),
                                          static_cast<double*>(raw_out), s);
   return fail(OPM_ERR_UNSUPPORTED, "adjoint dtype");
 }
 
 opm_status launch_mip_backward(const opm_plan* p, const float* g, const int32_t* argz,
                                float* g_raw, cudaStream_t s) {
-  return run<float, float, 4, true>(p, g, argz, g_raw, s);
+  const PlanView& v = p->view;
+  const long long nraw = (long long)v.nscan * v.nrows * v.ncols;
+  const int vec_ok = (nraw % 4 == 0) && ((uintptr_t)g_raw % 16 == 0);
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  const long long want = ((vec_ok ? nraw / 4 : nraw) + 255) / 256;
+  const int zgrid = (int)std::max(1LL, std::min<long long>(want, (long long)nsm * 8));
+  k_fill_zero<<<zgrid, 256, 0, s>>>(g_raw, nraw, vec_ok);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "launch k_fill_zero");
+  const long long gx = (v.nx + kScX - 1) / kScX, gy = (v.ny + kScY - 1) / kScY;
+  if (gx > 0x7fffffffLL || gy > 65535) return fail(OPM_ERR_UNSUPPORTED, "MIP backward grid exceeds launch limits");
+  if (gx == 0 || gy == 0) return OPM_OK;
+  k_mip_scatter<<<dim3((unsigned)gx, (unsigned)gy), dim3(kScX, kScY), 0, s>>>(v, g, argz, g_raw);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_mip_scatter");
 }
 
 }  // namespace opm

@@ -9,6 +9,8 @@ paper_2211_00645_gb300.profile_case ...``).
   --kernel sheet     the sheet-frame view with the shear of Eq. 1 (opm_sheet_project)
   --kernel pair      one plane-pair update of the plane-by-plane view (opm_stream_pair)
   --kernel batch1    the named stack alone through the persistent batch kernel
+  --kernel adjoint   skew adjoint of an FP32 volume (opm_skew_adjoint)
+  --kernel mipbwd    z-MIP backward scatter onto the raw grid (opm_mip_backward)
                      (--kchunk, --ctas: its launch shape)
   --nscan N          override the stack's scan-plane count (smaller captures)
 
@@ -33,7 +35,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["project", "deskew", "fused", "sheet", "pair", "batch", "batch1"], required=True)
+    ap.add_argument("--kernel", choices=["project", "deskew", "fused", "sheet", "pair", "batch", "batch1", "adjoint", "mipbwd"], required=True)
     ap.add_argument("--kchunk", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--config", default="liveview_200x512x2048")
@@ -85,6 +87,20 @@ def main(argv=None):
 
             def launch():
                 b.launch(args.ctas, s)
+        elif args.kernel in ("adjoint", "mipbwd"):
+            g = torch.Generator(device="cuda").manual_seed(1)
+            r = torch.empty(plan.raw_shape, device="cuda")
+            if args.kernel == "adjoint":
+                v = torch.randn(plan.vol_shape, generator=g, device="cuda")
+
+                def launch():
+                    opm.opm_skew_adjoint(plan, v, r, s)
+            else:
+                gz = torch.randn((plan.ny, plan.nx), generator=g, device="cuda")
+                argz = torch.randint(0, plan.nz, (plan.ny, plan.nx), generator=g, device="cuda", dtype=torch.int32)
+
+                def launch():
+                    opm.opm_mip_backward(plan, gz, argz, r, s)
         elif args.kernel == "pair":
             zmip = torch.zeros((plan.ny, plan.nx), device="cuda")
             ymip = torch.zeros((plan.nz, plan.nx), device="cuda")

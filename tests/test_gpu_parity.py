@@ -257,6 +257,27 @@ def test_mip_backward(lib, shape):
     assert_close(G.cpu().numpy(), O.mip_backward(gz.astype(np.float64), argz, g), what="mip backward")
 
 
+@pytest.mark.parametrize("shape", [(24, 6, 203, 30.0, 0.4, 0.115), SHAPES[4], SHAPES[5], SHAPES[9]])
+def test_mip_backward_collisions(lib, shape):
+    """Arbitrary arg-max rows, out-of-range ones included: few rows make many
+    columns j of one x feed the same raw sample.  The output buffer is
+    misaligned and pre-filled with NaN, so every sample must be written."""
+    g = O.geometry(*shape)
+    rng = np.random.default_rng(21)
+    gz = rng.standard_normal((g.ny, g.nx)).astype(np.float32)
+    argz = rng.integers(-1, g.nz + 1, size=(g.ny, g.nx)).astype(np.int32)
+    plan = lib.Plan(*shape)
+    n = int(np.prod(plan.raw_shape))
+    buf = torch.full((n + 1,), float("nan"), device="cuda")
+    G = buf[1:].view(plan.raw_shape)
+    lib.opm_mip_backward(plan, to_dev(gz, torch), to_dev(argz, torch), G)
+    torch.cuda.synchronize()
+    ref = O.mip_backward(gz.astype(np.float64), argz, g)
+    got = G.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert_close(got, ref, what=f"mip backward {shape}")
+
+
 def test_non_default_stream_and_no_allocation(lib):
     shape = SHAPES[0]
     R = _stack(shape)

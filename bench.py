@@ -293,6 +293,41 @@ def adjoint_bench(torch, opm, peak):
     return out
 
 
+def large_bench(torch, opm, peak):
+    """The large-volume workload 1000 x 1024 x 2048 uint16 (theta 45, step
+    0.2, pixel 0.115): the FP32 volume, the round-to-nearest uint16 volume and
+    the z-MIP written in one pass (opm_deskew_mip), timed with CUDA events
+    against raw + both volumes + z-MIP bytes."""
+    c = opm_synth.CONFIGS["large_1000x1024x2048"]
+    p = opm.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    s = torch.cuda.current_stream()
+    host = opm_synth.tiled_stack((c.nscan, c.nrows, c.ncols), seed=c.seed)
+    raw = torch.from_numpy(host.view(np.int16)).cuda().view(torch.uint16)
+    del host
+    vol = torch.empty(p.vol_shape, device="cuda")
+    vol16 = torch.empty(p.vol_shape, dtype=torch.int16, device="cuda").view(torch.uint16)
+    zmip = torch.empty((p.ny, p.nx), device="cuda")
+    nbytes = 2 * raw.numel() + 6 * vol.numel() + 4 * zmip.numel()
+    for _ in range(3):
+        opm.opm_deskew_mip(p, raw, vol, vol16, zmip, None, s)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = 10
+    e0.record(s)
+    for _ in range(n):
+        opm.opm_deskew_mip(p, raw, vol, vol16, zmip, None, s)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / n * 1e-3
+    out = {"workload": "large_1000x1024x2048", "grid": [p.nz, p.ny, p.nx],
+           "call": "opm_deskew_mip (FP32 volume + uint16 volume + z-MIP, one pass)", "bytes": nbytes,
+           "us": round(t * 1e6, 1), "GBps": round(nbytes / t / 1e9, 1), "frac": round(nbytes / t / 1e9 / peak, 4),
+           "volumes_per_s": round(1.0 / t, 2)}
+    del raw, vol, vol16, zmip
+    torch.cuda.empty_cache()
+    return out
+
+
 def rolling_bench(torch, opm, plan, host_raw, raw):
     """Frame-by-frame live view of the live-view stack (Fig. 4 rolling and
     global modes): every frame is copied in from pinned host memory and its
@@ -436,6 +471,7 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=256)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1000 x 1024 x 2048 one-pass volume")
     ap.add_argument("--serve-paced", type=int, default=200, help="stacks at Poisson arrivals (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-saturated", type=int, default=1800, help="stacks arriving at once (0: skip)")
@@ -626,6 +662,8 @@ def main():
     del sheet
     line["differentiable"] = adjoint_bench(torch, opm, peak)
     line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
+    if not args.no_large:
+        line["large_volume"] = large_bench(torch, opm, peak)
     if args.serve_paced > 0 or args.serve_saturated > 0:
         del vol, raw
         torch.cuda.empty_cache()

@@ -112,16 +112,23 @@ opm_status opm_deskew_dual(const opm_plan* plan, const void* raw, opm_dtype in_t
                            uint16_t* vol_u16, void* cuda_stream);
 
 /*
- * opm_deskew_mip - the volume and the live view in one pass over the raw
- * stack (the paper's remap followed by its maximum projection, Fig. 2c-d):
- * vol_f32 and/or vol_u16 [nz][ny][nx] as opm_deskew / opm_deskew_dual
- * write them, zmip [ny][nx] and ymip [nz][nx] as opm_project writes them
- * (either may be NULL), all bit-identical to those calls.  uint16 input on
- * plans the fast projection takes (pixel <= step, ny >= 32, rows of a
- * multiple of 16 bytes, 16-byte aligned raw) runs as one fused kernel that
- * stores every voxel as it folds it into the projections, plus a kernel
- * that zeroes the rows outside each tile's band; anything else runs the
- * separate calls.  Asynchronous; allocates nothing.
+ * opm_deskew_mip - the volume and the live view in one call (the paper's
+ * remap followed by its maximum projection, Fig. 2c-d): vol_f32 and/or
+ * vol_u16 [nz][ny][nx] as opm_deskew / opm_deskew_dual write them, zmip
+ * [ny][nx] and ymip [nz][nx] as opm_project writes them (either may be
+ * NULL), all bit-identical to those calls.
+ * By default the projection runs on the plan's own high-priority stream
+ * beside the volume on cuda_stream: it is forked from cuda_stream (an event
+ * recorded there) and joined back into it before the call returns, so work
+ * queued on cuda_stream afterwards sees every output; the pair is
+ * capturable into a CUDA graph.  The projection's persistent kernel then
+ * takes one CTA per SM, which leaves room on each SM for the write-bound
+ * volume kernel.  Calls on one plan are serialised on a host mutex for the
+ * fork and join.  A plan created with the environment variable
+ * OPM_ONE_PASS_FUSED=1 instead runs uint16 input through one fused kernel
+ * that stores every voxel as it folds it into the projections (raw read
+ * once), and FP32 input through the separate kernels on cuda_stream.
+ * Asynchronous; allocates nothing.
  * Errors: OPM_ERR_INVALID_ARG (NULL plan or raw, no volume), OPM_ERR_UNSUPPORTED
  * (input type, launch limits), OPM_ERR_CUDA.
  */

@@ -135,43 +135,76 @@ __device__ __forceinline__ float feed_weight(const PlanView& v, Split b, int jj,
   return 0.0f;
 }
 
+// A warp is one column j and 32 consecutive x.  Its lanes' arg-max rows
+// differ, and so do their search windows; the window scans therefore run
+// over offsets d from j, with warp-uniform trip counts (the warp's largest
+// window reach), so that every argz / g load is one coalesced row access and
+// the lanes stay converged.
 __global__ void __launch_bounds__(kScX* kScY)
 k_mip_scatter(PlanView v, const float* __restrict__ g, const int32_t* __restrict__ argz, float* __restrict__ g_raw) {
   const int x = blockIdx.x * kScX + threadIdx.x;
-  const int j = blockIdx.y * kScY + threadIdx.y;
-  if (x >= v.nx || j >= v.ny) return;
-  const int k = __ldg(argz + (size_t)j * v.nx + x);
-  if (k < 0 || k >= v.nz) return;  // feeds no raw sample
-  const Split b = v.B[k];
-  int n0;
-  float w;
+  const int j = blockIdx.y * kScY + threadIdx.y;  // warp-uniform
+  if (j >= v.ny) return;                          // whole warp
+  const bool in = x < v.nx;
+  const int k = in ? __ldg(argz + (size_t)j * v.nx + x) : -1;
+  const bool live = k >= 0 && k < v.nz;  // out-of-range rows feed no raw sample
+  const Split b = v.B[live ? k : 0];
+  int n0 = 0;
+  float w = 0.0f;
   plane_weight(v.A[j], b, v.linear, n0, w);
-#pragma unroll 1
+  // target t: plane n0 + t with weight wt[t]; own[t] while j may own it
+  const float wt[2] = {1.0f - w, w};
+  bool own[2];
+  int lo[2], hi[2];
+  int back = 0, fwd = 0;
+#pragma unroll
   for (int t = 0; t < 2; ++t) {
     const int n = n0 + t;
-    const float wj = t == 0 ? 1.0f - w : w;
-    if (n < 0 || n >= v.nscan || wj == 0.0f) continue;
-    int jlo, jhi;
-    j_window(v, b, n, jlo, jhi);
-    if (j < jlo || j > jhi) continue;
-    bool owner = true;
-#pragma unroll 1
-    for (int jj = jlo; jj < j; ++jj) {
-      if (__ldg(argz + (size_t)jj * v.nx + x) == k && feed_weight(v, b, jj, n) != 0.0f) {
-        owner = false;
-        break;
-      }
+    own[t] = live && n >= 0 && n < v.nscan && wt[t] != 0.0f;
+    lo[t] = hi[t] = j;
+    if (own[t]) {
+      j_window(v, b, n, lo[t], hi[t]);
+      own[t] = j >= lo[t] && j <= hi[t];
     }
-    if (!owner) continue;
-    float acc = fmaf(wj, __ldg(g + (size_t)j * v.nx + x), 0.0f);
-#pragma unroll 1
-    for (int jj = j + 1; jj <= jhi; ++jj) {
-      if (__ldg(argz + (size_t)jj * v.nx + x) != k) continue;
-      const float wt = feed_weight(v, b, jj, n);
-      if (wt != 0.0f) acc = fmaf(wt, __ldg(g + (size_t)jj * v.nx + x), acc);
+    if (own[t]) {
+      back = max(back, j - lo[t]);
+      fwd = max(fwd, hi[t] - j);
     }
-    g_raw[((size_t)n * v.nrows + k) * v.ncols + x] = acc;
   }
+  back = __reduce_max_sync(0xffffffffu, back);
+  fwd = __reduce_max_sync(0xffffffffu, fwd);
+  const int32_t* az = argz + x;
+  const float* gz = g + x;
+  // j owns plane n unless a smaller column of the window feeds it too
+#pragma unroll 1
+  for (int d = 1; d <= back; ++d) {
+    const int jj = j - d;
+    const bool c0 = own[0] && jj >= lo[0], c1 = own[1] && jj >= lo[1];
+    if ((c0 || c1) && __ldg(az + (size_t)jj * v.nx) == k) {
+      const float f0 = feed_weight(v, b, jj, n0), f1 = feed_weight(v, b, jj, n0 + 1);
+      if (c0 && f0 != 0.0f) own[0] = false;
+      if (c1 && f1 != 0.0f) own[1] = false;
+    }
+  }
+  const float gj = (own[0] || own[1]) ? __ldg(gz + (size_t)j * v.nx) : 0.0f;
+  float acc[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) acc[t] = fmaf(wt[t], gj, 0.0f);
+  // the owner sums every feeding column in ascending j
+#pragma unroll 1
+  for (int d = 1; d <= fwd; ++d) {
+    const int jj = j + d;
+    const bool c0 = own[0] && jj <= hi[0], c1 = own[1] && jj <= hi[1];
+    if ((c0 || c1) && __ldg(az + (size_t)jj * v.nx) == k) {
+      const float gv = __ldg(gz + (size_t)jj * v.nx);
+      const float f0 = feed_weight(v, b, jj, n0), f1 = feed_weight(v, b, jj, n0 + 1);
+      if (c0 && f0 != 0.0f) acc[0] = fmaf(f0, gv, acc[0]);
+      if (c1 && f1 != 0.0f) acc[1] = fmaf(f1, gv, acc[1]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+    if (own[t]) g_raw[((size_t)(n0 + t) * v.nrows + k) * v.ncols + x] = acc[t];
 }
 
 __global__ void k_fill_zero(float* __restrict__ p, long long n, int vec_ok) {

@@ -327,9 +327,41 @@ opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t
 
 namespace opm {
 
+namespace {
+
+// The volume on the caller's stream s and the live view beside it on the
+// plan's high-priority side stream, forked from and joined back into s.
+// The live view's persistent kernel takes a quarter of its usual grid (one
+// CTA per SM), so each SM also holds volume CTAs: the issue-bound projection
+// then fills the issue slots the write-bound volume leaves idle.  Each
+// kernel computes exactly what it computes alone.
+opm_status deskew_beside_project(const opm_plan* p, const void* raw, opm_dtype in_t, float* volf, uint16_t* volh,
+                                 float* zmip, float* ymip, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(p->side_mu);
+  cudaError_t e = cudaEventRecord(p->fork_ev, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork_ev, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "forking the live view onto the side stream");
+  opm_status st = launch_project(p, raw, in_t, zmip, nullptr, ymip, nullptr, p->side, 4);
+  opm_status sv = OPM_OK;
+  if (volf && volh)
+    sv = launch_deskew_dual(p, raw, in_t, volf, volh, s);
+  else
+    sv = launch_deskew(p, raw, in_t, volf ? (void*)volf : (void*)volh, volf ? OPM_F32 : OPM_U16, s);
+  // join even after a failed launch, so that s never runs ahead of the side stream
+  e = cudaEventRecord(p->join_ev, p->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join_ev, 0);
+  if (st != OPM_OK) return st;
+  if (sv != OPM_OK) return sv;
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "joining the side stream");
+}
+
+}  // namespace
+
 opm_status launch_deskew_mip(const opm_plan* p, const void* raw, opm_dtype in_t, float* volf, uint16_t* volh,
                              float* zmip, float* ymip, cudaStream_t s) {
   const PlanView& v = p->view;
+  if ((zmip || ymip) && p->side && !p->one_pass_fused)
+    return deskew_beside_project(p, raw, in_t, volf, volh, zmip, ymip, s);
   if (in_t != OPM_U16) {
     // FP32 input: the volume, then the projections
     opm_status st = OPM_OK;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -100,15 +101,27 @@ struct opm_plan {
   int device;        // -1: created without a device
   void* dmem;        // one allocation holding every device table
   opm::PlanView view;
+  // opm_deskew_mip: the live view runs on `side` (highest priority, a
+  // quarter of the persistent grid) beside the volume on the caller's stream,
+  // forked and joined through the two events; one_pass_fused selects the
+  // single fused kernel instead (environment OPM_ONE_PASS_FUSED=1 at plan
+  // creation).  `side` is NULL for a plan made without a device.
+  int one_pass_fused = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  mutable std::mutex side_mu;  // one fork/join on `side` at a time
 };
 
 namespace opm {
 
 // Kernel launchers (one per translation unit).  Each returns OPM_OK or an
 // error already recorded with fail()/cuda_fail().
+// grid_div > 1 launches the persistent fast kernel with 1/grid_div of its
+// CTAs (each then walks grid_div of the schedule's lists), leaving room on
+// every SM for a kernel that runs beside it.
 opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t,
                           float* zmip, float* zsum, float* ymip, int32_t* argz,
-                          cudaStream_t s);
+                          cudaStream_t s, int grid_div = 1);
 opm_status launch_deskew(const opm_plan* p, const void* raw, opm_dtype in_t,
                          void* vol, opm_dtype out_t, cudaStream_t s);
 opm_status launch_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32,

@@ -123,6 +123,8 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
   p->interp = interp;
   const char* fg = std::getenv("OPM_FORCE_GENERIC");
   p->force_generic = (fg && fg[0] == '1') ? 1 : 0;
+  const char* of = std::getenv("OPM_ONE_PASS_FUSED");
+  p->one_pass_fused = (of && of[0] == '1') ? 1 : 0;
   p->device = -1;
   p->dmem = nullptr;
 
@@ -305,6 +307,18 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
     delete p;
     return cuda_fail(e, "uploading plan tables");
   }
+  int pri_lo = 0, pri_hi = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&pri_lo, &pri_hi)) != cudaSuccess ||
+      (e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, pri_hi)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming)) != cudaSuccess) {
+    if (p->join_ev) cudaEventDestroy(p->join_ev);
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->side) cudaStreamDestroy(p->side);
+    cudaFree(p->dmem);
+    delete p;
+    return cuda_fail(e, "creating the plan's side stream");
+  }
   p->device = dev;
   PlanView& v = p->view;
   v.A = dA;
@@ -348,6 +362,9 @@ opm_status opm_plan_destroy(opm_plan* p) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
+    if (p->join_ev) cudaEventDestroy(p->join_ev);
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->side) cudaStreamDestroy(p->side);
     cudaError_t e = cudaFree(p->dmem);
     if (cur != p->device && cur >= 0) cudaSetDevice(cur);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaFree(plan tables)");

@@ -480,14 +480,15 @@ opm_status prepare_kernel(K kern, int dev, int* done) {
 }
 
 opm_status launch_fast(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, int tiles,
-                       cudaStream_t s) {
+                       cudaStream_t s, int grid_div) {
   static int done[64] = {0};
   opm_status st = prepare_kernel(k_project_fast, p->device, done);
   if (st != OPM_OK) return st;
   const PlanView& v = p->view;
   if (!v.units || !v.lists) return fail(OPM_ERR_INTERNAL, "plan has no fast-kernel schedule");
-  const int grid = std::min(v.nunits, v.nlists);
-  if (grid == 0) return OPM_OK;
+  const int full = std::min(v.nunits, v.nlists);
+  if (full == 0) return OPM_OK;
+  const int grid = std::max(1, full / std::max(1, grid_div));
   k_project_fast<<<grid, kThreads, fast::total(args.P), s>>>(map, args);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_fast");
@@ -511,7 +512,7 @@ opm_status launch_gen(const opm_plan* p, const CUtensorMap& map, const ProjArgs&
 }  // namespace
 
 opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, float* zmip, float* zsum,
-                          float* ymip, int32_t* argz, cudaStream_t s) {
+                          float* ymip, int32_t* argz, cudaStream_t s, int grid_div) {
   const PlanView& v = p->view;
   const bool u16 = in_t == OPM_U16;
   const size_t es = u16 ? 2 : 4;
@@ -571,7 +572,7 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
   opm_status st = u16 ? encode_raw<uint16_t>(v, raw, P, &map) : encode_raw<float>(v, raw, P, &map);
   if (st != OPM_OK) return st;
   const int jtiles = (v.ny + kTileJ - 1) / kTileJ;
-  if (fast) return launch_fast(p, map, args, jtiles, s);
+  if (fast) return launch_fast(p, map, args, jtiles, s, grid_div);
   return u16 ? launch_gen<uint16_t>(p, map, args, jtiles, s) : launch_gen<float>(p, map, args, jtiles, s);
 }
 

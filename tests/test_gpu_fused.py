@@ -1,7 +1,10 @@
-"""Volume and live view in one pass (opm_deskew_mip): the FP32 and uint16
+"""Volume and live view in one call (opm_deskew_mip): the FP32 and uint16
 volumes and the z-MIP / y-MIP equal the separate opm_deskew /
-opm_deskew_dual / opm_project calls bit for bit, on plans the fused kernel
-takes and on plans that fall back to the separate kernels."""
+opm_deskew_dual / opm_project calls bit for bit, in both of its modes: the
+live view beside the volume on the plan's side stream (default) and the
+single fused kernel (plans created with OPM_ONE_PASS_FUSED=1)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -17,6 +20,18 @@ SHAPES = [(64, 128, 128, 30.0, 0.4, 0.115),     # fused
           (40, 70, 136, 35.0, 0.3, 0.1),        # fused, nx not a multiple of 128
           (16, 20, 64, 35.0, 0.05, 0.1),        # pixel > step: separate kernels
           (12, 9, 30, 90.0, 0.1, 0.1)]          # rows of 60 bytes: separate kernels
+
+
+MODES = ["beside", "fused"]
+
+
+def _plan(lib, shape, mode):
+    if mode == "fused":
+        os.environ["OPM_ONE_PASS_FUSED"] = "1"
+    try:
+        return lib.Plan(*shape)
+    finally:
+        os.environ.pop("OPM_ONE_PASS_FUSED", None)
 
 
 def _stack(shape, seed=4):
@@ -35,10 +50,11 @@ def _fused(lib, plan, raw, f32=True, u16=True, z=True, y=True):
     return vf, vh, zm, ym
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_fused_equals_separate_calls(lib, shape):
+def test_fused_equals_separate_calls(lib, shape, mode):
     R = _stack(shape)
-    plan = lib.Plan(*shape)
+    plan = _plan(lib, shape, mode)
     raw = to_dev(R, torch)
     vf, vh, zm, ym = _fused(lib, plan, raw)
     ref_f = lib.deskew(plan, raw)
@@ -53,11 +69,12 @@ def test_fused_equals_separate_calls(lib, shape):
     assert_close(vf.cpu().numpy(), V, what="fused volume")
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("outs", [(True, False, True, False), (False, True, False, True), (True, False, False, False)])
-def test_fused_output_subsets(lib, outs):
+def test_fused_output_subsets(lib, outs, mode):
     shape = SHAPES[0]
     R = _stack(shape, seed=9)
-    plan = lib.Plan(*shape)
+    plan = _plan(lib, shape, mode)
     raw = to_dev(R, torch)
     vf, vh, zm, ym = _fused(lib, plan, raw, *outs)
     ref = lib.project(plan, raw, zmip=True, ymip=True)
@@ -71,10 +88,11 @@ def test_fused_output_subsets(lib, outs):
         assert torch.equal(ym, ref["ymip"])
 
 
-def test_fused_liveview_full_size(lib):
+@pytest.mark.parametrize("mode", MODES)
+def test_fused_liveview_full_size(lib, mode):
     c = opm_synth.CONFIGS["liveview_200x512x2048"]
     R = opm_synth.tiled_stack((c.nscan, c.nrows, c.ncols), seed=2)
-    plan = lib.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    plan = _plan(lib, (c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel), mode)
     raw = to_dev(R, torch)
     vf, _, zm, ym = _fused(lib, plan, raw, u16=False)
     ref = lib.project(plan, raw, zmip=True, ymip=True)
@@ -89,3 +107,65 @@ def test_fused_argument_checks(lib):
     with pytest.raises(lib.OpmError) as e:
         lib.opm_deskew_mip(plan, raw, None, None, torch.empty((plan.ny, plan.nx), device="cuda"), None)
     assert e.value.status == lib.OPM_ERR_INVALID_ARG
+
+
+def test_beside_joins_the_callers_stream(lib):
+    """Work queued on the caller's stream after the call sees the finished
+    live view (the side stream is joined back), on a non-default stream,
+    call after call."""
+    shape = (120, 256, 512, 35.0, 0.3, 0.1)
+    R = opm_synth.tiled_stack(shape[:3], seed=5)
+    plan = lib.Plan(*shape)
+    raw = to_dev(R, torch)
+    ref = lib.project(plan, raw, zmip=True, ymip=True)
+    ref_v = lib.deskew(plan, raw)
+    vf = torch.empty(plan.vol_shape, device="cuda")
+    zm = torch.empty((plan.ny, plan.nx), device="cuda")
+    ym = torch.empty((plan.nz, plan.nx), device="cuda")
+    s = torch.cuda.Stream()
+    lib.opm_deskew_mip(plan, raw, vf, None, zm, ym, s)      # first call loads the modules
+    s.synchronize()
+    copies = []
+    with torch.cuda.stream(s):
+        for _ in range(4):
+            zm.fill_(-1.0)
+            ym.fill_(-1.0)
+            lib.opm_deskew_mip(plan, raw, vf, None, zm, ym, s)
+            copies.append((zm.clone(), ym.clone()))
+    s.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        lib.opm_deskew_mip(plan, raw, vf, None, zm, ym, s)
+    s.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, "opm_deskew_mip allocated device memory"
+    for z, y in copies:
+        assert torch.equal(z, ref["zmip"]) and torch.equal(y, ref["ymip"])
+    assert torch.equal(vf, ref_v)
+    lib.opm_plan_check(plan)
+
+
+def test_beside_in_a_cuda_graph(lib):
+    """The fork onto the side stream and the join back are capturable: a
+    graph of the call replays to the same outputs."""
+    shape = SHAPES[0]
+    R = _stack(shape, seed=6)
+    plan = lib.Plan(*shape)
+    raw = to_dev(R, torch)
+    vf = torch.empty(plan.vol_shape, device="cuda")
+    zm = torch.empty((plan.ny, plan.nx), device="cuda")
+    ym = torch.empty((plan.nz, plan.nx), device="cuda")
+    s = torch.cuda.Stream()
+    lib.opm_deskew_mip(plan, raw, vf, None, zm, ym, s)
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        lib.opm_deskew_mip(plan, raw, vf, None, zm, ym, s)
+    zm.zero_()
+    ym.zero_()
+    vf.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    ref = lib.project(plan, raw, zmip=True, ymip=True)
+    assert torch.equal(zm, ref["zmip"]) and torch.equal(ym, ref["ymip"])
+    assert torch.equal(vf, lib.deskew(plan, raw))

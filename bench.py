@@ -48,14 +48,12 @@ KERNEL_SOURCES = {
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per full-size
 # launch from ncu captures, keyed by the hash of the kernel's sources at
-# capture time (reported as null once a source has changed).  liveview:
-# captured at full size (200 x 512 x 2048): 450.97 MB read + 7.79 MB written.
-# volume_f32: captured with 100 scan planes (213.17 MB read, 2963.44 MB
-# written) and scaled to 200 planes, reads by the raw bytes (x2.0) and writes
-# by the volume bytes (x1.4161).
+# capture time (reported as null once a source has changed).  volume_f32:
+# captured with 100 scan planes (213.06 MB read, 2962.89 MB written) and
+# scaled to 200 planes, reads by the raw bytes (x2.0) and writes by the
+# volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "liveview": {"src_sha": "7e772d5d56c5", "bytes_per_launch": 458759424},
-    "volume_f32": {"src_sha": "c434b066b408", "bytes_per_launch": 4622831132},
+    "volume_f32": {"src_sha": "2dab9b812885", "bytes_per_launch": 4621842793},
 }
 
 

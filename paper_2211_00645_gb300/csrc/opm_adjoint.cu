@@ -5,9 +5,12 @@
 // (weight 1 - w) or n - 1 (weight w), in ascending j.  The weights are
 // computed with the forward kernels' own split-table formula, so the adjoint
 // is the exact transpose of the map the forward kernels apply.  No atomics:
-// results are bitwise reproducible.  The adjoint gathers per raw sample; the
-// z-MIP backward, whose input is non-zero on one row per column, scatters.
+// results are bitwise reproducible.  The FP32 adjoint walks the columns j of
+// a row once per block of planes; the FP64 adjoint (gradient checks) gathers
+// per raw sample; the z-MIP backward, whose input is non-zero on one row per
+// column, scatters.  All three sum every plane's terms in ascending j.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "opm_common.cuh"
@@ -235,13 +238,147 @@ opm_status run(const opm_plan* p, const T* src, T* dst, cudaStream_t s) {
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch adjoint gather");
 }
 
+// ------------------------------------------------------- adjoint, walking j
+//
+// A warp owns kWalkPlanes consecutive raw planes [na, nb) of one row k, its
+// lanes 4 columns x each.  It walks the output columns j that can feed those
+// planes once, in ascending j, reading each V[k][j][x..x+3] once and adding
+// it into the two planes its tent touches.  n0(j, k) never decreases along
+// j, so the planes complete in order: the warp holds two accumulators
+// (planes p and p + 1) and stores a plane as soon as the walk has passed it.
+// Every plane takes the same terms in the same order as in the gather above,
+// so the two agree bit for bit.  Control flow is uniform across the warp
+// (n0 and w depend on j and k only), every load and store is one 512-byte
+// row.
+constexpr int kWalkPlanes = 16;
+constexpr int kWalkWarps = 4;
+constexpr int kWalkUnroll = 2;
+
+template <typename T, typename Acc, int VEC>
+__device__ __forceinline__ void walk_store(const PlanView& v, T* __restrict__ raw, int k, int x0, bool vec, int lim,
+                                           int n, const Acc (&acc)[VEC]) {
+  T* op = raw + ((size_t)n * v.nrows + k) * v.ncols + x0;
+  if (vec) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(op) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    } else {
+      *reinterpret_cast<double2*>(op) = make_double2(acc[0], acc[1]);
+    }
+  } else {
+    for (int i = 0; i < VEC && i < lim; ++i) op[i] = (T)acc[i];
+  }
+}
+
+template <typename T, typename Acc, int VEC>
+__global__ void __launch_bounds__(kThreadsX* kWalkWarps)
+k_adjoint_walk(PlanView v, const T* __restrict__ vol, T* __restrict__ raw, int xtiles, int vec_ok) {
+  const int k = blockIdx.x / xtiles;
+  const int xt = blockIdx.x - k * xtiles;
+  const int x0 = (xt * kThreadsX + threadIdx.x) * VEC;
+  const int na = (blockIdx.y * kWalkWarps + threadIdx.y) * kWalkPlanes;
+  if (x0 >= v.nx || na >= v.nscan) return;
+  const int nb = min(na + kWalkPlanes, v.nscan);
+  const int lim = v.nx - x0;
+  const bool vec = vec_ok && lim >= VEC;
+  const Split b = v.B[k];
+  int jlo, jhi, dummy;
+  j_window(v, b, na, jlo, dummy);
+  j_window(v, b, nb - 1, dummy, jhi);
+  const Acc zero[VEC] = {};
+  Acc lo[VEC], hi[VEC];  // planes p and p + 1
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) lo[i] = hi[i] = Acc(0);
+  int p = na - 1;  // no plane of [na, nb) below p + 1 holds a contribution yet
+  int nw = na;     // next plane of [na, nb) to store
+  // store plane q (when it is this warp's) after zeros for any skipped planes
+  auto flush = [&](int q, const Acc(&acc)[VEC]) {
+    if (q < na || q >= nb) return;
+    for (; nw < q; ++nw) walk_store<T, Acc, VEC>(v, raw, k, x0, vec, lim, nw, zero);
+    walk_store<T, Acc, VEC>(v, raw, k, x0, vec, lim, q, acc);
+    nw = q + 1;
+  };
+  const T* vp = vol + (size_t)k * v.ny * v.nx + x0;
+  // kWalkUnroll columns per step: their weights first, then their loads (all
+  // in flight together), then their terms in ascending j
+#pragma unroll 1
+  for (int j0 = jlo; j0 <= jhi; j0 += kWalkUnroll) {
+    int n0s[kWalkUnroll];
+    Acc ws[kWalkUnroll], val[kWalkUnroll][VEC];
+    bool tl[kWalkUnroll], th[kWalkUnroll];
+#pragma unroll
+    for (int u = 0; u < kWalkUnroll; ++u) {
+      const int j = j0 + u;
+      n0s[u] = INT_MIN;
+      ws[u] = Acc(0);
+      tl[u] = th[u] = false;
+      if (j <= jhi) {
+        plane_weight_t<Acc>(v.A[j], b, v.linear, n0s[u], ws[u]);
+        const int n0 = n0s[u];
+        tl[u] = n0 >= na && n0 < nb && Acc(1) - ws[u] != Acc(0);
+        th[u] = n0 + 1 >= na && n0 + 1 < nb && ws[u] != Acc(0);
+      }
+      if (tl[u] || th[u]) load_vec<T, VEC, Acc>(vp + (size_t)j * v.nx, vec, lim, val[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kWalkUnroll; ++u) {
+      const int n0 = n0s[u];
+      if (n0 == INT_MIN) break;  // past jhi
+      if (n0 < p) {  // only before the first plane of [na, nb): n0 never decreases along j
+        if (n0 + 1 >= na) atomicOr(v.err, kErrOrder);
+        continue;
+      }
+      if (n0 > p) {
+        flush(p, lo);
+        if (n0 == p + 1) {
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) {
+            lo[i] = hi[i];
+            hi[i] = Acc(0);
+          }
+        } else {
+          flush(p + 1, hi);
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) lo[i] = hi[i] = Acc(0);
+        }
+        p = n0;
+      }
+      if (tl[u]) {
+        const Acc wl = Acc(1) - ws[u];
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) lo[i] = fma(wl, val[u][i], lo[i]);
+      }
+      if (th[u]) {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) hi[i] = fma(ws[u], val[u][i], hi[i]);
+      }
+    }
+  }
+  flush(p, lo);
+  flush(p + 1, hi);
+  for (; nw < nb; ++nw) walk_store<T, Acc, VEC>(v, raw, k, x0, vec, lim, nw, zero);
+}
+
+template <typename T, typename Acc, int VEC>
+opm_status run_walk(const opm_plan* p, const T* src, T* dst, cudaStream_t s) {
+  const PlanView& v = p->view;
+  const int xtiles = (v.nx + kThreadsX * VEC - 1) / (kThreadsX * VEC);
+  const long long gx = (long long)xtiles * v.nz;
+  const long long groups = (v.nscan + kWalkPlanes - 1) / kWalkPlanes;
+  const long long gy = (groups + kWalkWarps - 1) / kWalkWarps;
+  if (gx > 0x7fffffffLL || gy > 65535) return fail(OPM_ERR_UNSUPPORTED, "adjoint grid exceeds launch limits");
+  const int vec_ok = (v.nx % VEC == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
+  k_adjoint_walk<T, Acc, VEC><<<dim3((unsigned)gx, (unsigned)gy), dim3(kThreadsX, kWalkWarps), 0, s>>>(
+      v, src, dst, xtiles, vec_ok);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_adjoint_walk");
+}
+
 }  // namespace
 
 opm_status launch_adjoint(const opm_plan* p, const void* vol, void* raw_out, opm_dtype t,
                           cudaStream_t s) {
   if (t == OPM_F32)
-    return run<float, float, 4, 2, 2>(p, static_cast<const float*>(vol),
-                                       static_cast<float*>(raw_out), s);
+    return run_walk<float, float, 4>(p, static_cast<const float*>(vol), static_cast<float*>(raw_out), s);
   if (t == OPM_F64)
     return run<double, double, 2, 1, 1>(p, static_cast<const double*>(vol),
                                          static_cast<double*>(raw_out), s);

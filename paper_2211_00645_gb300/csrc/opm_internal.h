@@ -59,6 +59,7 @@ enum : unsigned {
   kErrSlabRange = 1u,   // a plane offset fell outside the staged slab
   kErrWaitTimeout = 2u, // an mbarrier wait gave up
   kErrSearch = 4u,      // a column search of the plane-pair kernel ran past its bound
+  kErrOrder = 8u,       // the adjoint walk met a lower plane that decreased along j
 };
 
 void set_error(const std::string& msg);

@@ -211,7 +211,26 @@ def test_adjoint_f32(lib, shape):
     plan = lib.Plan(*shape)
     G = lib.skew_adjoint(plan, to_dev(y, torch))
     torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
     assert_close(G.cpu().numpy(), O.skew_adjoint(y.astype(np.float64), g), what="adjoint")
+
+
+@pytest.mark.parametrize("shape", [(19, 6, 7, 30.0, 0.4, 0.115), (9, 5, 7, 35.0, 0.05, 0.1),
+                                   (12, 4, 9, 20.0, 0.7, 0.1)])
+@pytest.mark.parametrize("interp", [0, 1])
+def test_adjoint_f32_explicit_transpose(lib, shape, interp):
+    """Tiny plans, LINEAR and NEAREST, ragged plane groups and columns: the
+    adjoint against the transpose of the oracle's entry-by-entry matrix, and
+    no device error flag raised."""
+    g = O.geometry(*shape)
+    y = opm_synth.gaussian((g.nz, g.ny, g.nx), 12, np.float32)
+    plan = lib.Plan(*shape, interp=interp)
+    G = lib.skew_adjoint(plan, to_dev(y, torch))
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    A = O.explicit_matrix(g, interp)
+    ref = (A.T @ y.astype(np.float64).ravel()).reshape(g.nscan, g.nrows, g.ncols)
+    assert_close(G.cpu().numpy(), ref, what=f"adjoint vs explicit transpose {shape} interp {interp}")
 
 
 @pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[5], SHAPES[6]])

@@ -5,10 +5,10 @@
 // (weight 1 - w) or n - 1 (weight w), in ascending j.  The weights are
 // computed with the forward kernels' own split-table formula, so the adjoint
 // is the exact transpose of the map the forward kernels apply.  No atomics:
-// results are bitwise reproducible.  The FP32 adjoint walks the columns j of
-// a row once per block of planes; the FP64 adjoint (gradient checks) gathers
-// per raw sample; the z-MIP backward, whose input is non-zero on one row per
-// column, scatters.  All three sum every plane's terms in ascending j.
+// results are bitwise reproducible.  The adjoint walks the columns j of a
+// row once per block of planes; the z-MIP backward, whose input is non-zero
+// on one row per column, scatters.  Both sum every raw sample's terms in
+// ascending j, skipping zero weights.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -20,7 +20,6 @@ namespace opm {
 namespace {
 
 constexpr int kThreadsX = 32;
-constexpr int kThreadsY = 8;
 
 // Search window of columns j whose tent can reach plane n in row k.
 __device__ __forceinline__ void j_window(const PlanView& v, Split b, int n, int& jlo, int& jhi) {
@@ -31,88 +30,6 @@ __device__ __forceinline__ void j_window(const PlanView& v, Split b, int n, int&
   jhi = min(v.ny - 1, (int)ceilf(hi) + 2);
 }
 
-// kPlanes consecutive planes n per thread share one walk over j; kUnroll
-// columns j have their loads issued together.
-template <typename T, typename Acc, int VEC, int kPlanes, int kUnroll>
-__global__ void __launch_bounds__(kThreadsX* kThreadsY)
-k_gather_t(PlanView v, const T* __restrict__ src, T* __restrict__ dst, int xtiles, int vec_ok) {
-  const int k = blockIdx.x / xtiles;
-  const int xt = blockIdx.x - k * xtiles;
-  const int x0 = (xt * kThreadsX + threadIdx.x) * VEC;
-  const int nb = (blockIdx.y * kThreadsY + threadIdx.y) * kPlanes;  // first plane of this thread
-  if (x0 >= v.nx || nb >= v.nscan) return;
-  const int lim = v.nx - x0;
-  const bool vec = vec_ok && lim >= VEC;
-  const Split b = v.B[k];
-  int jlo, jhi, dummy;
-  j_window(v, b, nb, jlo, dummy);
-  j_window(v, b, min(nb + kPlanes - 1, v.nscan - 1), dummy, jhi);
-
-  Acc acc[kPlanes][VEC];
-#pragma unroll
-  for (int q = 0; q < kPlanes; ++q)
-#pragma unroll
-    for (int i = 0; i < VEC; ++i) acc[q][i] = Acc(0);
-
-  // plane nb + q takes (1 - w) from columns with n0 == nb + q and w from
-  // columns with n0 + 1 == nb + q, each plane in ascending j.  Columns are
-  // taken kUnroll at a time so that their loads are in flight together.
-#pragma unroll 1
-  for (int j0 = jlo; j0 <= jhi; j0 += kUnroll) {
-    Acc val[kUnroll][VEC], ws[kUnroll];
-    int q0s[kUnroll];
-    bool ul[kUnroll], uh[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int j = j0 + u;
-      ul[u] = uh[u] = false;
-      q0s[u] = 0;
-      ws[u] = Acc(0);
-      if (j <= jhi) {
-        int n0;
-        Acc w;
-        plane_weight_t<Acc>(v.A[j], b, v.linear, n0, w);
-        const int q0 = n0 - nb;  // plane index taking 1 - w; q0 + 1 takes w
-        q0s[u] = q0;
-        ws[u] = w;
-        ul[u] = q0 >= 0 && q0 < kPlanes && Acc(1) - w != Acc(0);
-        uh[u] = q0 + 1 >= 0 && q0 + 1 < kPlanes && w != Acc(0);
-      }
-      if (ul[u] || uh[u]) load_vec<T, VEC, Acc>(src + ((size_t)k * v.ny + j) * v.nx + x0, vec, lim, val[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-#pragma unroll
-      for (int q = 0; q < kPlanes; ++q) {
-        if (ul[u] && q == q0s[u]) {
-          const Acc wl = Acc(1) - ws[u];
-#pragma unroll
-          for (int i = 0; i < VEC; ++i) acc[q][i] = fma(wl, val[u][i], acc[q][i]);
-        }
-        if (uh[u] && q == q0s[u] + 1) {
-#pragma unroll
-          for (int i = 0; i < VEC; ++i) acc[q][i] = fma(ws[u], val[u][i], acc[q][i]);
-        }
-      }
-    }
-  }
-
-#pragma unroll
-  for (int q = 0; q < kPlanes; ++q) {
-    if (nb + q >= v.nscan) break;
-    T* op = dst + ((size_t)(nb + q) * v.nrows + k) * v.ncols + x0;
-    if (vec) {
-      if constexpr (sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(op) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
-      } else {
-        *reinterpret_cast<double2*>(op) = make_double2(acc[q][0], acc[q][1]);
-      }
-    } else {
-      for (int i = 0; i < VEC && i < lim; ++i) op[i] = (T)acc[q][i];
-    }
-  }
-}
-
 // ---------------------------------------------------------------- z-MIP backward
 //
 // The z-MIP gradient reaches the raw grid only through the arg-max row of
@@ -121,9 +38,8 @@ k_gather_t(PlanView v, const T* __restrict__ src, T* __restrict__ dst, int xtile
 // then fills the one or two samples it feeds, (n0, k, x) with 1 - w and
 // (n0 + 1, k, x) with w, k = argz[j][x].  Several columns j of one x can
 // feed the same sample; its smallest such j (inside the sample's search
-// window) owns it and sums every feeding column in ascending j, the same
-// terms in the same order as the gather above, so the result is the same bit
-// for bit, without atomics.
+// window) owns it and sums every feeding column in ascending j (the
+// transpose's terms, in the adjoint's order), without atomics.
 
 constexpr int kScX = 32;  // lanes along x (coalesced argz / g reads)
 constexpr int kScY = 8;   // columns j per CTA (one per warp)
@@ -222,22 +138,6 @@ __global__ void k_fill_zero(float* __restrict__ p, long long n, int vec_ok) {
   for (; i < n; i += stride) p[i] = 0.0f;
 }
 
-template <typename T, typename Acc, int VEC, int kPlanes, int kUnroll>
-opm_status run(const opm_plan* p, const T* src, T* dst, cudaStream_t s) {
-  const PlanView& v = p->view;
-  const int xtiles = (v.nx + kThreadsX * VEC - 1) / (kThreadsX * VEC);
-  const long long gx = (long long)xtiles * v.nz;
-  const long long gy = (v.nscan + kThreadsY * kPlanes - 1) / (kThreadsY * kPlanes);
-  if (gx > 0x7fffffffLL || gy > 65535)
-    return fail(OPM_ERR_UNSUPPORTED, "adjoint grid exceeds launch limits");
-  const int vec_ok = (v.nx % VEC == 0) && ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
-  dim3 block(kThreadsX, kThreadsY);
-  dim3 grid((unsigned)gx, (unsigned)gy);
-  k_gather_t<T, Acc, VEC, kPlanes, kUnroll><<<grid, block, 0, s>>>(v, src, dst, xtiles, vec_ok);
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch adjoint gather");
-}
-
 // ------------------------------------------------------- adjoint, walking j
 //
 // A warp owns kWalkPlanes consecutive raw planes [na, nb) of one row k, its
@@ -246,10 +146,9 @@ opm_status run(const opm_plan* p, const T* src, T* dst, cudaStream_t s) {
 // it into the two planes its tent touches.  n0(j, k) never decreases along
 // j, so the planes complete in order: the warp holds two accumulators
 // (planes p and p + 1) and stores a plane as soon as the walk has passed it.
-// Every plane takes the same terms in the same order as in the gather above,
-// so the two agree bit for bit.  Control flow is uniform across the warp
-// (n0 and w depend on j and k only), every load and store is one 512-byte
-// row.
+// A plane's sum runs over its window's columns in ascending j, zero weights
+// skipped.  Control flow is uniform across the warp (n0 and w depend on j
+// and k only), and every load and store is one row of the warp's lanes.
 constexpr int kWalkPlanes = 16;
 constexpr int kWalkWarps = 4;
 constexpr int kWalkUnroll = 2;
@@ -380,8 +279,7 @@ opm_status launch_adjoint(const opm_plan* p, const void* vol, void* raw_out, opm
   if (t == OPM_F32)
     return run_walk<float, float, 4>(p, static_cast<const float*>(vol), static_cast<float*>(raw_out), s);
   if (t == OPM_F64)
-    return run<double, double, 2, 1, 1>(p, static_cast<const double*>(vol),
-                                         static_cast<double*>(raw_out), s);
+    return run_walk<double, double, 2>(p, static_cast<const double*>(vol), static_cast<double*>(raw_out), s);
   return fail(OPM_ERR_UNSUPPORTED, "adjoint dtype");
 }
 

@@ -187,6 +187,11 @@ def _ptr(t, shape=None, name="tensor"):
         return None
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    dev = _torch().cuda.current_device()
+    if t.device.index != dev:
+        # the plan lives on the current device; a kernel there must not be
+        # handed another GPU's memory
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if shape is not None and tuple(t.shape) != tuple(shape):

@@ -270,6 +270,25 @@ def test_mip_backward_matches_finite_differences():
     np.testing.assert_allclose(G, fd, rtol=1e-6, atol=1e-7)
 
 
+@pytest.mark.parametrize("shape", [(6, 4, 3, 30.0, 0.4, 0.115), (5, 3, 2, 35.0, 0.05, 0.1)])
+def test_mip_backward_equals_masked_explicit_transpose(shape):
+    """Any arg-max map, out-of-range rows included: the z-MIP backward is the
+    transpose of the entry-by-entry matrix applied to g placed at (argz, j, x)
+    (rows outside [0, nz) place nothing)."""
+    g = O.geometry(*shape)
+    rng = np.random.default_rng(71)
+    gz = rng.standard_normal((g.ny, g.nx))
+    argz = rng.integers(-1, g.nz + 1, size=(g.ny, g.nx))
+    Y = np.zeros((g.nz, g.ny, g.nx))
+    for j in range(g.ny):
+        for x in range(g.nx):
+            if 0 <= argz[j, x] < g.nz:
+                Y[argz[j, x], j, x] = gz[j, x]
+    A = O.explicit_matrix(g)
+    ref = (A.T @ Y.ravel()).reshape(g.nscan, g.nrows, g.ncols)
+    np.testing.assert_allclose(O.mip_backward(gz, argz, g), ref, rtol=1e-12, atol=1e-12)
+
+
 def test_adjoint_matches_finite_differences():
     g = O.geometry(4, 3, 2, 35.0, 0.3, 0.1)
     R = _rand((g.nscan, g.nrows, g.ncols), 61)

@@ -25,6 +25,13 @@ def _pins_pass():
         zmip, zsum, ymip, argz = O.project(R, g)
         ok &= np.array_equal(zmip, V.max(0)) and np.array_equal(argz, np.argmax(V, 0))
         ok &= np.allclose(zsum, V.sum(0)) and np.array_equal(ymip, V.max(1))
+        # z-MIP backward: the transpose applied to g placed at (argz, j, x)
+        gz = opm_synth.gaussian((g.ny, g.nx), 9)
+        az = np.random.default_rng(10).integers(-1, g.nz + 1, size=(g.ny, g.nx))
+        Yg = np.zeros((g.nz, g.ny, g.nx))
+        jj, xx = np.nonzero((az >= 0) & (az < g.nz))
+        Yg[az[jj, xx], jj, xx] = gz[jj, xx]
+        ok &= np.allclose(O.mip_backward(gz, az, g).reshape(-1), A.T @ Yg.reshape(-1), atol=1e-12)
     # single bright voxel at its Eq. (1) column
     g = O.geometry(64, 128, 4, 30.0, 0.4, 0.115)
     R = opm_synth.bright_voxel((64, 128, 4), 20, 70, 2)
@@ -89,6 +96,21 @@ def _shifted_adjoint(V, g):
     return G
 
 
+def _mip_backward_next_row(gz, argz, g):
+    gz = np.asarray(gz, dtype=np.float64)
+    G = np.empty((g.nscan, g.nrows, g.ncols))
+    for k in range(g.nz):
+        G[:, k, :] = M._tent_matrix(g, k) @ np.where(np.asarray(argz) + 1 == k, gz, 0.0)
+    return G
+
+
+_real_mip_backward = M.mip_backward
+
+
+def _mip_backward_clipped_rows(gz, argz, g):
+    return _real_mip_backward(gz, np.clip(argz, 0, g.nz - 1), g)
+
+
 @pytest.mark.parametrize("target,mutant", [
     ("plane_coord", _wrong_shear_sign),
     ("deskew_row", _swapped_weights),
@@ -96,6 +118,8 @@ def _shifted_adjoint(V, g):
     ("geometry", _j0_off_by_one),
     ("project", _last_occurrence_project),
     ("skew_adjoint", _shifted_adjoint),
+    ("mip_backward", _mip_backward_next_row),
+    ("mip_backward", _mip_backward_clipped_rows),
 ])
 def test_pins_catch_mutant(monkeypatch, target, mutant):
     monkeypatch.setattr(M, target, mutant)

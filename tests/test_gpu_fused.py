@@ -101,6 +101,21 @@ def test_fused_liveview_full_size(lib, mode):
     assert torch.equal(vf.max(dim=0).values, zm)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_fused_f32_input(lib, mode):
+    """FP32 raw input: the volumes and projections equal the separate calls."""
+    shape = SHAPES[2]
+    R = _stack(shape, seed=11).astype(np.float32)
+    plan = _plan(lib, shape, mode)
+    raw = to_dev(R, torch)
+    vf, vh, zm, ym = _fused(lib, plan, raw)
+    ref = lib.project(plan, raw, zmip=True, ymip=True)
+    torch.cuda.synchronize()
+    assert torch.equal(vf, lib.deskew(plan, raw))
+    assert torch.equal(vh.view(torch.int16), lib.deskew(plan, raw, out_dtype=torch.uint16).view(torch.int16))
+    assert torch.equal(zm, ref["zmip"]) and torch.equal(ym, ref["ymip"])
+
+
 def test_fused_argument_checks(lib):
     plan = lib.Plan(*SHAPES[0])
     raw = torch.zeros(plan.raw_shape, dtype=torch.uint16, device="cuda")

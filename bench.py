@@ -3,7 +3,9 @@
 Workload (one step): the 200 scan planes x 512 rows x 2048 columns uint16
 stack (theta 35 deg, step 0.3 um, pixel 0.1 um, Poisson(100) + 2000 blobs):
   1. the fused live view: deskew + z-MIP + y-MIP, no volume in memory;
-  2. the full FP32 deskewed volume (512 x 1021 x 2048).
+  2. the full FP32 deskewed volume (512 x 1021 x 2048);
+both from one opm_deskew_mip call, whose two kernels run side by side.  Each
+kernel is also timed alone, for the per-kernel table and the roofline.
 Metric: deskew GB/s of algorithmic bytes (raw read once + every output written
 once), with the fraction of the measured HBM copy bandwidth, and volumes/s.
 
@@ -114,6 +116,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            self.f.close()
+            os.unlink(self.f.name)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.1)
         self.proc.terminate()

@@ -341,7 +341,7 @@ opm_status deskew_beside_project(const opm_plan* p, const void* raw, opm_dtype i
   cudaError_t e = cudaEventRecord(p->fork_ev, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork_ev, 0);
   if (e != cudaSuccess) return cuda_fail(e, "forking the live view onto the side stream");
-  opm_status st = launch_project(p, raw, in_t, zmip, nullptr, ymip, nullptr, p->side, 4);
+  opm_status st = launch_project(p, raw, in_t, zmip, nullptr, ymip, nullptr, p->side, p->lists_per_sm);
   opm_status sv = OPM_OK;
   if (volf && volh)
     sv = launch_deskew_dual(p, raw, in_t, volf, volh, s);

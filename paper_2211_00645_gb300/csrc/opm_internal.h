@@ -54,6 +54,20 @@ struct __align__(16) FastRow {
 };
 static_assert(sizeof(FastRow) == 288, "FastRow is copied as 288 bytes");
 
+// Plans whose lower plane advances by p/q planes per output column j
+// (pixel/step = p/q) take the periodic live-view kernel (opm_periodic.cuh):
+// along a camera row, the 32 columns of a tile sit on planes
+// floor((t p + ph)/q) above the first one, t = 0..31, for one phase ph in
+// [0, q).  One kernel is compiled per entry of this list; any other plan
+// takes k_project_fast.
+struct Family {
+  int p, q;
+};
+constexpr Family kFamilies[] = {{1, 3}};
+constexpr int kNumFamilies = (int)(sizeof(kFamilies) / sizeof(kFamilies[0]));
+constexpr int kPerCtasPerSm = 5;  // its persistent CTAs per SM
+__host__ __device__ constexpr int per_ofs(int p, int q, int ph, int t) { return (t * p + ph) / q; }
+
 // Error bits recorded by kernels in the plan's device error word.
 enum : unsigned {
   kErrSlabRange = 1u,   // a plane offset fell outside the staged slab
@@ -92,6 +106,9 @@ struct opm_plan {
   int force_generic;  // use the plain (non-TMA) kernels for every call
   int P;              // planes staged per row for a 32-column tile
   int fast_ok;        // full tiles never step more than one plane per column
+  int family = 0;     // 1 + index into kFamilies when the periodic kernel applies, else 0
+  int lists_per_sm = 4;  // persistent CTA lists per SM of the live-view schedule
+  int per_variant = 0;
   std::vector<opm::Split> hA, hB;
   std::vector<opm::Band> hBand;
   std::vector<float> hYinit;

@@ -198,13 +198,61 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
           }
           for (int g = 0; g < 4; ++g) {
             unsigned adv = 0;
-            for (int jj = 1; jj < 8; ++jj)
+            for (int jj = 1; jj < 8; ++jj) {
               if (o[8 * g + jj] == o[8 * g + jj - 1] + 1) adv |= 1u << jj;
+              // the fast kernel takes a row's y-max over the first and last
+              // column of each plane interval only, which needs the weights
+              // to grow along j inside an interval
+              if (o[8 * g + jj] == o[8 * g + jj - 1] && fr.w[8 * g + jj][0] < fr.w[8 * g + jj - 1][0])
+                p->fast_ok = 0;
+            }
             fr.rec[g].adv = adv;
             fr.rec[g].ofirst = o[8 * g];
           }
           p->hFnlo[t * nrows + k] = nlo;
         }
+      }
+      if (!p->fast_ok) {
+        p->hFrow.clear();
+        p->hFnlo.clear();
+      }
+    }
+    // The periodic kernel: the first compiled p/q for which every row of
+    // every tile steps through its planes as floor((t p + ph) / q),
+    // t = 0..31; the phase of each 8-column chunk goes into bits 16..23 of
+    // its step word.
+    const char* np = std::getenv("OPM_NO_PERIODIC");
+    if (p->fast_ok && !(np && np[0] == '1')) {
+      // plane of column t (0..31) of a tile row, relative to column 0
+      auto tile_ofs = [](const FastRow& fr, int t) {
+        const FastRec& rc = fr.rec[t / 8];
+        const unsigned below = rc.adv & ((2u << (t % 8)) - 1u) & 0xffu;  // steps at or before column t % 8
+        return rc.ofirst + __builtin_popcount(below) - fr.rec[0].ofirst;
+      };
+      auto phase = [&](const FastRow& fr, int fp, int fq) {
+        for (int ph = 0; ph < fq; ++ph) {
+          bool same = true;
+          for (int t = 1; same && t < kTileJ; ++t) same = tile_ofs(fr, t) == per_ofs(fp, fq, ph, t);
+          if (same) return ph;
+        }
+        return -1;
+      };
+      for (int f = 0; f < kNumFamilies && !p->family; ++f) {
+        bool all = true;
+        for (size_t i = 0; all && i < p->hFrow.size(); ++i)
+          all = phase(p->hFrow[i], kFamilies[f].p, kFamilies[f].q) >= 0;
+        if (all) p->family = f + 1;
+      }
+      if (p->family) {
+        const int fp = kFamilies[p->family - 1].p, fq = kFamilies[p->family - 1].q;
+        for (FastRow& fr : p->hFrow) {
+          const int ph = phase(fr, fp, fq);
+          for (int g = 0; g < 4; ++g) fr.rec[g].adv |= (unsigned)((8 * g * fp + ph) % fq) << 16;
+        }
+        const char* pv = std::getenv("OPM_PER_VARIANT");
+        p->per_variant = pv ? std::atoi(pv) & 3 : 0;
+        static const int lps[4] = {4, 6, 5, 5};
+        p->lists_per_sm = lps[p->per_variant];
       }
     }
 
@@ -257,7 +305,7 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
         }
       }
       if (p->hUnits.size() > (size_t)INT32_MAX) p->fast_ok = 0;
-      const int nlists = std::min(std::max(nsm, 1) * 4, kMaxLists);
+      const int nlists = std::min(std::max(nsm, 1) * p->lists_per_sm, kMaxLists);
       p->hLists.assign(nlists + 1, 0);
       schedule_lpt(p->hUnits.data(), (int)p->hUnits.size(), nlists, p->hLists.data());
     } catch (const std::bad_alloc&) {

@@ -42,7 +42,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "opm_tma.cuh"
+#include "opm_periodic.cuh"
 
 namespace opm {
 
@@ -105,6 +105,55 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
       ok = fast_consume(jb, ring, g, v.err, warp - 1, lane);
   }
   if (warp == 0) fast_drain(ring, g, ok, v.err);
+}
+
+// Periodic kernel (opm_periodic.cuh): the fast kernel's schedule, tables
+// and TMA ring for plans with pixel/step = Pp/Qq, with straight-line compute
+// warps per phase pair; MINB CTAs per SM, S ring stages.
+template <int Pp, int Qq, int MINB, int S>
+__global__ void __launch_bounds__(per::kThreads, MINB)
+k_project_per(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
+  const PlanView& v = args.v;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const PerRing ring = per_ring(smem, S, args.P);
+  per_ring_init(ring);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  int g = 0;
+  bool ok = true;
+  int l = (int)blockIdx.x - (int)gridDim.x;
+  int u = 0, uend = 0;
+#pragma unroll 1
+  while (ok) {
+    if (u >= uend) {
+      do {
+        l += gridDim.x;
+        if (l >= v.nlists) break;
+        u = v.lists[l];
+        uend = v.lists[l + 1];
+      } while (u >= uend);
+      if (u >= uend) break;
+    }
+    const WorkUnit un = v.units[u++];
+    FastJob jb;
+    jb.ks = un.ks;
+    jb.ke = un.ke;
+    jb.tmap = &tmap;
+    jb.rows = v.frow + (size_t)un.jt * v.nz;
+    jb.nlos = v.fnlo + (size_t)un.jt * v.nz;
+    jb.zmip = args.zmip;
+    jb.ymip = args.ymip;
+    jb.nz = v.nz;
+    jb.nx = v.nx;
+    jb.j0 = tile_j0(un.jt, v.ny);
+    jb.xbase = un.xt * kX;
+    jb.P = args.P;
+    if (warp == 0)
+      ok = per_produce(jb, ring, g, v.err, lane);
+    else
+      ok = per_consume<Pp, Qq>(jb, ring, g, v.err, warp - 1, lane);
+  }
+  if (warp == 0) per_drain(ring, g, ok, v.err);
 }
 
 // =====================================================================
@@ -479,9 +528,50 @@ opm_status prepare_kernel(K kern, int dev, int* done) {
   return OPM_OK;
 }
 
+// The periodic kernel of the plan's family.
+template <int F>
+opm_status launch_per_f(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, cudaStream_t s,
+                        int grid_div) {
+  if constexpr (F < kNumFamilies) {
+    if (p->family - 1 != F) return launch_per_f<F + 1>(p, map, args, s, grid_div);
+    constexpr int Pp = kFamilies[F].p, Qq = kFamilies[F].q;
+    static int done[4][64] = {{0}};
+    const int pv = p->per_variant & 3;
+    opm_status st = pv == 0   ? prepare_kernel(k_project_per<Pp, Qq, 4, 6>, p->device, done[0])
+                    : pv == 1 ? prepare_kernel(k_project_per<Pp, Qq, 6, 4>, p->device, done[1])
+                    : pv == 2 ? prepare_kernel(k_project_per<Pp, Qq, 5, 5>, p->device, done[2])
+                              : prepare_kernel(k_project_per<Pp, Qq, 5, 4>, p->device, done[3]);
+    if (st != OPM_OK) return st;
+    const PlanView& v = p->view;
+    const int full = std::min(v.nunits, v.nlists);
+    if (full == 0) return OPM_OK;
+    const int grid = std::max(1, full / std::max(1, grid_div));
+    const int P = args.P;
+    if (pv == 0)
+      k_project_per<Pp, Qq, 4, 6><<<grid, per::kThreads, per::total(6, P), s>>>(map, args);
+    else if (pv == 1)
+      k_project_per<Pp, Qq, 6, 4><<<grid, per::kThreads, per::total(4, P), s>>>(map, args);
+    else if (pv == 2)
+      k_project_per<Pp, Qq, 5, 5><<<grid, per::kThreads, per::total(5, P), s>>>(map, args);
+    else
+      k_project_per<Pp, Qq, 5, 4><<<grid, per::kThreads, per::total(4, P), s>>>(map, args);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_per");
+  } else {
+    return fail(OPM_ERR_INTERNAL, "plan names an unknown periodic family");
+  }
+}
+
+opm_status launch_per(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, cudaStream_t s,
+                      int grid_div) {
+  if (!p->view.units || !p->view.lists) return fail(OPM_ERR_INTERNAL, "plan has no fast-kernel schedule");
+  return launch_per_f<0>(p, map, args, s, grid_div);
+}
+
 opm_status launch_fast(const opm_plan* p, const CUtensorMap& map, const ProjArgs& args, int tiles,
                        cudaStream_t s, int grid_div) {
   static int done[64] = {0};
+  if (p->family) return launch_per(p, map, args, s, grid_div);
   opm_status st = prepare_kernel(k_project_fast, p->device, done);
   if (st != OPM_OK) return st;
   const PlanView& v = p->view;
@@ -521,7 +611,8 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
   const bool tma_ok = !p->force_generic && encode_fn() != nullptr && ((uintptr_t)raw % 16 == 0) &&
                       ((size_t)v.ncols * es) % 16 == 0 && P <= 256;
   const bool gen_ok = tma_ok && (int)(u16 ? gen::total<uint16_t>(P) : gen::total<float>(P)) <= smax;
-  const bool fast = gen_ok && u16 && !zsum && !argz && p->fast_ok && v.frow && (int)fast::total(P) <= smax;
+  const bool fast = gen_ok && u16 && !zsum && !argz && p->fast_ok && v.frow &&
+                    (int)(p->family ? per::total(6, P) : fast::total(P)) <= smax;
 
   if (!gen_ok) {
     const long long nzx = (long long)v.ny * v.nx, nyx = (long long)v.nz * v.nx;

@@ -83,6 +83,24 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
 opm_status opm_plan_shape(const opm_plan* plan, int64_t* nz, int64_t* ny,
                           int64_t* nx, int64_t* j0);
 
+/*
+ * opm_plan_path - which live-view kernel opm_project runs for this plan with
+ * uint16 input, z-MIP and/or y-MIP outputs and no z-sum or arg-max (the
+ * serving outputs).  A diagnostic of the plan; it computes nothing.
+ *   *path = OPM_PATH_PERIODIC: the periodic kernel for pixel/step = p/q,
+ *           chosen when every 32-column tile row steps through its planes as
+ *           floor((t p + ph) / q) (Eq. 1 with a rational scan-to-pixel ratio;
+ *           checked with the kernels' own arithmetic); *fam_p, *fam_q = p, q.
+ *   *path = OPM_PATH_FAST: the fast kernel (pixel <= step, ny >= 32).
+ *   *path = OPM_PATH_GENERAL: the general kernel (any plan; also every call
+ *           with z-sum or arg-max output, or FP32 input).
+ * Any output pointer may be NULL.  Errors: OPM_ERR_INVALID_ARG (plan NULL).
+ * The raw stack's alignment is not known here; opm_project takes the plain
+ * kernels when a row is not a multiple of 16 bytes or raw is misaligned.
+ */
+typedef enum { OPM_PATH_GENERAL = 0, OPM_PATH_FAST = 1, OPM_PATH_PERIODIC = 2 } opm_path;
+opm_status opm_plan_path(const opm_plan* plan, int* path, int* fam_p, int* fam_q);
+
 /* Frees a plan and its device tables.  NULL is accepted.  The caller must not
  * destroy a plan while work that uses it is still queued on a stream. */
 opm_status opm_plan_destroy(opm_plan* plan);
@@ -344,13 +362,17 @@ opm_status opm_batch_destroy(opm_batch* b);
  * hot path).
  *
  * The first call on each device does set-up (looks up the device array's
- * address with that device current, sets the kernel's shared-memory limit);
- * make it before any stream capture.  The host array is copied with
- * pageable cudaMemcpyAsync, which returns once the data is staged, so the
- * call blocks for prior work on cuda_stream.  There is one host array and
- * one device array per device: calls that overlap, from several threads or
- * on several streams of one device, race and corrupt each other's work
- * lists; serialise them (consecutive calls on one stream are safe).
+ * address with that device current, sets the kernel's shared-memory limit).
+ * The work list is built in one host array shared by the whole process and
+ * copied with a pageable cudaMemcpyAsync; the call holds a process-wide lock
+ * from building the list until that copy returns (once its source is
+ * staged), so threads driving different devices may call it at once.  The
+ * call must never be captured in a CUDA graph: on a capturing stream it
+ * returns OPM_ERR_UNSUPPORTED and launches nothing.  There is one device
+ * array per device: calls whose kernels overlap on one device (several
+ * streams, or several threads on one device) race on it and corrupt each
+ * other's work lists; serialise them (consecutive calls on one stream are
+ * safe).
  * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED, OPM_ERR_CUDA,
  * OPM_ERR_INTERNAL (check only).
  */

@@ -43,6 +43,7 @@ _SIGS = {
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "opm_plan_shape": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4),
+    "opm_plan_path": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3),
     "opm_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_deskew": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p]),
@@ -158,6 +159,18 @@ def opm_plan_shape(plan: Plan):
     v = [ctypes.c_int64() for _ in range(4)]
     _check(load().opm_plan_shape(plan.handle, *[ctypes.byref(x) for x in v]), "opm_plan_shape")
     return tuple(int(x.value) for x in v)
+
+
+OPM_PATH_GENERAL, OPM_PATH_FAST, OPM_PATH_PERIODIC = 0, 1, 2
+
+
+def opm_plan_path(plan: Plan):
+    """``opm_plan_path``: (path, p, q) of the live-view kernel the plan takes
+    (OPM_PATH_GENERAL / _FAST / _PERIODIC; p/q = pixel/step of the periodic
+    kernel, else 0, 0)."""
+    v = [ctypes.c_int() for _ in range(3)]
+    _check(load().opm_plan_path(plan.handle, *[ctypes.byref(x) for x in v]), "opm_plan_path")
+    return tuple(x.value for x in v)
 
 
 def opm_plan_destroy(plan: Plan):

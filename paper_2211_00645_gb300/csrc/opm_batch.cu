@@ -30,7 +30,7 @@
 #include <string>
 
 #include "opm_sched.h"
-#include "opm_tma.cuh"
+#include "opm_periodic.cuh"
 
 namespace opm {
 
@@ -140,6 +140,66 @@ k_batch_fast(const unsigned char* __restrict__ wl, int Pl, unsigned* err) {
   if (warp == 0) fast_drain(ring, g, ok, err);
 }
 
+// The same persistent loop with the periodic kernel's producer and compute
+// warps (opm_periodic.cuh), for batches whose items all belong to the plan
+// family pixel/step = Pp/Qq.
+template <int Pp, int Qq>
+__global__ void __launch_bounds__(per::Cfg<kPerRun>::kThreads, kPerCtasPerSm)
+k_batch_per(const unsigned char* __restrict__ wl, int Pl, unsigned* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(wl);
+  const PerRing ring = per_ring(smem, kPerStages, Pl);
+  per_ring_init(ring, per::Cfg<kPerRun>::kCW);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  int g = 0;
+  bool ok = true;
+  int l = (int)blockIdx.x - (int)gridDim.x;
+  int u = 0, uend = 0;
+#pragma unroll 1
+  while (ok) {
+    if (u >= uend) {
+      const int* lists = reinterpret_cast<const int*>(wl + hdr->off_lists);
+      do {
+        l += gridDim.x;
+        if (l >= hdr->n_lists) break;
+        u = lists[l];
+        uend = lists[l + 1];
+      } while (u >= uend);
+      if (u >= uend) break;
+    }
+    const WorkUnit un = reinterpret_cast<const WorkUnit*>(wl + hdr->off_units)[u++];
+    const BatchItemDev* items = reinterpret_cast<const BatchItemDev*>(wl + kOffItems);
+    const BatchItemDev* it = items + un.item;
+    FastJob jb;
+    jb.tmap = &it->tmap;
+    jb.nz = it->nz;
+    jb.nx = it->nx;
+    jb.rows = it->frow + (size_t)un.jt * jb.nz;
+    jb.nlos = it->fnlo + (size_t)un.jt * jb.nz;
+    jb.zmip = it->zmip;
+    jb.ymip = it->ymip;
+    jb.j0 = tile_j0(un.jt, it->ny);
+    jb.xbase = un.xt * kX;
+    jb.ks = un.ks;
+    jb.ke = un.ke;
+    jb.P = it->P;
+    if (warp == 0) {
+      // the descriptor was written by a host copy: order it for the TMA unit
+      if (lane == 0)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(jb.tmap) : "memory");
+      __syncwarp();
+      ok = per_produce(jb, ring, g, err, lane);
+    } else {
+      ok = per_consume<kPerRun, Pp, Qq>(jb, ring, g, err, warp - 1, lane);
+    }
+  }
+  if (warp == 0) per_drain(ring, g, ok, err);
+}
+
+// Shared memory of a batch launch for slab depth Pl (family 0: k_batch_fast).
+size_t batch_smem(int Pl, int family) { return family ? per::total(kPerStages, Pl) : fast::total(Pl); }
+
 PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -159,6 +219,7 @@ PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
 struct WorkList {
   size_t used;  // bytes of the image to copy
   int n_items, n_units, n_segs, n_lists, Pl;
+  int family;  // kFamilies index + 1 shared by every item, or 0
 };
 
 // Builds the work-list image of `items` into `stage` (room for max_items
@@ -183,7 +244,7 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
   int* hlists = reinterpret_cast<int*>(stage + off_lists);
   WorkUnit* hunits = reinterpret_cast<WorkUnit*>(stage + off_units);
   int64_t nunits = 0;
-  int Pl = 2, nseg = 0;
+  int Pl = 2, nseg = 0, family = -1;
   for (int i = 0; i < n_items; ++i) {
     const opm_batch_item& it = items[i];
     const opm_plan* p = it.plan;
@@ -221,6 +282,7 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
     d.nx = (int)p->nx;
     d.P = p->P;
     Pl = std::max(Pl, p->P);
+    family = (family < 0 || family == p->family) ? p->family : 0;
     if (it.zmip) hsegs[nseg++] = BatchSeg{it.zmip, (long long)(p->ny * p->nx)};
     if (it.ymip) hsegs[nseg++] = BatchSeg{it.ymip, (long long)(p->nz * p->nx)};
     if (!it.zmip && !it.ymip) continue;
@@ -254,6 +316,7 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
   out->n_segs = nseg;
   out->n_lists = nlists;
   out->Pl = Pl;
+  out->family = family < 0 ? 0 : family;
   return OPM_OK;
 }
 
@@ -261,21 +324,48 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
 // header lists, so one grid shape serves every content.
 constexpr int kZeroRows = 32;
 
+template <int F>
+void launch_batch_per(const unsigned char* dev_wl, int Pl, int family, int grid, unsigned* err, cudaStream_t s) {
+  if constexpr (F < kNumFamilies) {
+    if (family - 1 != F) return launch_batch_per<F + 1>(dev_wl, Pl, family, grid, err, s);
+    k_batch_per<kFamilies[F].p, kFamilies[F].q>
+        <<<grid, per::Cfg<kPerRun>::kThreads, batch_smem(Pl, family), s>>>(dev_wl, Pl, err);
+  }
+}
+
 // Zero kernel, then `grid` persistent CTAs (none when grid == 0), on `s`.
-cudaError_t launch_worklist(const unsigned char* dev_wl, int Pl, int grid, unsigned* err, cudaStream_t s) {
+cudaError_t launch_worklist(const unsigned char* dev_wl, int Pl, int family, int grid, unsigned* err,
+                            cudaStream_t s) {
   k_batch_zero<<<dim3(64, kZeroRows), 256, 0, s>>>(dev_wl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || grid == 0) return e;
-  k_batch_fast<<<grid, kThreads, fast::total(Pl), s>>>(dev_wl, Pl, err);
+  if (family)
+    launch_batch_per<0>(dev_wl, Pl, family, grid, err, s);
+  else
+    k_batch_fast<<<grid, kThreads, fast::total(Pl), s>>>(dev_wl, Pl, err);
   return cudaGetLastError();
 }
 
-cudaError_t set_fast_attrs(int smem_optin) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+template <typename K>
+cudaError_t set_kernel_smem(K kern, int smem_optin) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_batch_fast, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   return e;
+}
+
+template <int F>
+cudaError_t set_per_attrs(int smem_optin) {
+  if constexpr (F < kNumFamilies) {
+    cudaError_t e = set_kernel_smem(k_batch_per<kFamilies[F].p, kFamilies[F].q>, smem_optin);
+    return e == cudaSuccess ? set_per_attrs<F + 1>(smem_optin) : e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t set_fast_attrs(int smem_optin) {
+  cudaError_t e = set_kernel_smem(k_batch_fast, smem_optin);
+  return e == cudaSuccess ? set_per_attrs<0>(smem_optin) : e;
 }
 
 }  // namespace
@@ -298,8 +388,8 @@ struct opm_batch {
   WorkList wl;           // the prepared content
   int attr_set;
   cudaStream_t capture;  // private stream the graph is captured on
-  cudaGraphExec_t graph; // zero + persistent kernels for (graph_Pl, graph_grid)
-  int graph_Pl, graph_grid, graph_captures;
+  cudaGraphExec_t graph; // zero + persistent kernels for (graph_Pl, graph_family, graph_grid)
+  int graph_Pl, graph_family, graph_grid, graph_captures;
 };
 
 extern "C" {
@@ -334,7 +424,7 @@ opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out) {
     return st;
   }
   std::memset(b->host, 0, kOffItems);
-  b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2};
+  b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2, 0};
   *out = b;
   return OPM_OK;
 }
@@ -369,7 +459,7 @@ opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items,
   if (st != OPM_OK) {
     // leave an empty, valid image behind
     std::memset(b->host, 0, kOffItems);
-    b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2};
+    b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2, 0};
     return st;
   }
   b->wl = wl;
@@ -389,7 +479,7 @@ opm_status opm_batch_upload(opm_batch* b, void* stream) {
 static opm_status batch_prepare_launch(opm_batch* b, int& ctas_per_sm) {
   if (ctas_per_sm < 0 || ctas_per_sm > 4) return fail(OPM_ERR_INVALID_ARG, "ctas_per_sm must lie in [0, 4]");
   if (ctas_per_sm == 0) ctas_per_sm = 4;
-  if ((int)fast::total(b->wl.Pl) > b->smem_optin)
+  if ((int)batch_smem(b->wl.Pl, b->wl.family) > b->smem_optin)
     return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
   if (!b->attr_set) {
     cudaError_t e = set_fast_attrs(b->smem_optin);
@@ -404,7 +494,7 @@ opm_status opm_batch_launch(opm_batch* b, int ctas_per_sm, void* stream) {
   opm_status st = batch_prepare_launch(b, ctas_per_sm);
   if (st != OPM_OK) return st;
   const int grid = (int)std::min<int64_t>(b->wl.n_units, (int64_t)b->nsm * ctas_per_sm);
-  cudaError_t e = launch_worklist(b->dev, b->wl.Pl, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
+  cudaError_t e = launch_worklist(b->dev, b->wl.Pl, b->wl.family, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
                                   static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "opm_batch_launch");
 }
@@ -414,7 +504,7 @@ opm_status opm_batch_launch_graph(opm_batch* b, int ctas_per_sm, void* stream) {
   opm_status st = batch_prepare_launch(b, ctas_per_sm);
   if (st != OPM_OK) return st;
   const int grid = b->nsm * ctas_per_sm;  // every CTA reads the unit count from the device header
-  if (!b->graph || b->graph_Pl != b->wl.Pl || b->graph_grid != grid) {
+  if (!b->graph || b->graph_Pl != b->wl.Pl || b->graph_family != b->wl.family || b->graph_grid != grid) {
     if (b->graph) {
       cudaError_t e = cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -423,7 +513,7 @@ opm_status opm_batch_launch_graph(opm_batch* b, int ctas_per_sm, void* stream) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaError_t le = launch_worklist(b->dev, b->wl.Pl, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
+    cudaError_t le = launch_worklist(b->dev, b->wl.Pl, b->wl.family, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
                                      b->capture);
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess) e = le;
@@ -434,6 +524,7 @@ opm_status opm_batch_launch_graph(opm_batch* b, int ctas_per_sm, void* stream) {
       return cuda_fail(e, "capturing the batch launch");
     }
     b->graph_Pl = b->wl.Pl;
+    b->graph_family = b->wl.family;
     b->graph_grid = grid;
     b->graph_captures += 1;
   }
@@ -445,7 +536,7 @@ opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, in
   if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
   if (n_items) *n_items = b->wl.n_items;
   if (n_units) *n_units = b->wl.n_units;
-  if (smem_bytes) *smem_bytes = (int)fast::total(b->wl.Pl);
+  if (smem_bytes) *smem_bytes = (int)batch_smem(b->wl.Pl, b->wl.family);
   if (graph_captures) *graph_captures = b->graph_captures;
   return OPM_OK;
 }
@@ -532,22 +623,33 @@ extern "C" opm_status opm_batch_project_static(const opm_batch_item* items, int 
   StaticDevice* sd = nullptr;
   opm_status st = static_setup(dev, &sd);
   if (st != OPM_OK) return st;
-  WorkList wl;
-  st = build_worklist(items, n_items, kchunk, dev, std::min(sd->nsm * 4, kMaxLists), g_static_stage, kStaticItems,
-                      kStaticUnits, "static work list", &wl);
-  if (st != OPM_OK) return st;
-  if ((int)fast::total(wl.Pl) > sd->smem_optin)
-    return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
-  // Pageable host -> device copy: it returns once its source has been
-  // staged, so the host image may be rebuilt by the next call.
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The host image is one array for the whole process and is copied with a
+  // pageable copy, which a stream capture cannot record: refuse capture.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(OPM_ERR_UNSUPPORTED, "opm_batch_project_static cannot be captured in a CUDA graph");
+  WorkList wl;
   unsigned char* dv = sd->scratch;
   unsigned* err = reinterpret_cast<unsigned*>(dv + kSBytes);
-  e = cudaMemcpyAsync(dv, g_static_stage, wl.used, cudaMemcpyHostToDevice, s);
+  {
+    // Build and copy under the lock: threads driving other devices share
+    // the host image.  The pageable copy returns once its source has been
+    // staged, so the image may be rebuilt as soon as it returns.
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    st = build_worklist(items, n_items, kchunk, dev, std::min(sd->nsm * 4, kMaxLists), g_static_stage, kStaticItems,
+                        kStaticUnits, "static work list", &wl);
+    if (st != OPM_OK) return st;
+    if ((int)batch_smem(wl.Pl, wl.family) > sd->smem_optin)
+      return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
+    e = cudaMemcpyAsync(dv, g_static_stage, wl.used, cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);  // error word starts at 0
   if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static upload");
   const int grid = (int)std::min<int64_t>(wl.n_units, (int64_t)sd->nsm * ctas_per_sm);
-  e = launch_worklist(dv, wl.Pl, grid, err, s);
+  e = launch_worklist(dv, wl.Pl, wl.family, grid, err, s);
   if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static launch");
   if (check) {
     unsigned word = 0;

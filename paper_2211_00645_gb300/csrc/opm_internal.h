@@ -65,7 +65,9 @@ struct Family {
 };
 constexpr Family kFamilies[] = {{1, 3}};
 constexpr int kNumFamilies = (int)(sizeof(kFamilies) / sizeof(kFamilies[0]));
-constexpr int kPerCtasPerSm = 5;  // its persistent CTAs per SM
+constexpr int kPerRun = 32;       // columns j per compute warp of the periodic kernel
+constexpr int kPerCtasPerSm = 4;  // its persistent CTAs per SM
+constexpr int kPerStages = 6;     // its TMA ring depth
 __host__ __device__ constexpr int per_ofs(int p, int q, int ph, int t) { return (t * p + ph) / q; }
 
 // Error bits recorded by kernels in the plan's device error word.
@@ -108,7 +110,6 @@ struct opm_plan {
   int fast_ok;        // full tiles never step more than one plane per column
   int family = 0;     // 1 + index into kFamilies when the periodic kernel applies, else 0
   int lists_per_sm = 4;  // persistent CTA lists per SM of the live-view schedule
-  int per_variant = 0;
   std::vector<opm::Split> hA, hB;
   std::vector<opm::Band> hBand;
   std::vector<float> hYinit;

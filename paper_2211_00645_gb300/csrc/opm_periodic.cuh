@@ -31,17 +31,25 @@ namespace {
 
 namespace per {
 
-constexpr int kCW = 2;                  // compute warps per CTA
-constexpr int kThreads = 32 * (kCW + 1);
 constexpr int kXL = 2;                  // columns x per lane
 constexpr int kXW = 32 * kXL;           // columns x per compute warp
-static_assert(kXW * kCW == kX, "two compute warps cover the 128-column x-tile");
+constexpr int kXH = kX / kXW;           // x-halves of the 128-column x-tile
+constexpr int kMaxCW = 4;               // compute warps per CTA at most
+
+// A compute warp owns a run of RUN columns j (16 or 32) for kXW columns x.
+template <int RUN>
+struct Cfg {
+  static_assert(RUN == 16 || RUN == 32, "runs of 16 or 32 columns");
+  static constexpr int kRuns = kTileJ / RUN;       // column runs per tile
+  static constexpr int kCW = kRuns * kXH;          // compute warps per CTA
+  static constexpr int kThreads = 32 * (kCW + 1);
+};
 
 // Shared memory for S stages of slab depth P.
 __host__ __device__ inline size_t off_tab(int S, int P) { return S * fast::stage_slab_bytes(P); }  // FastRow [S][2]
 __host__ __device__ inline size_t off_bar(int S, int P) { return off_tab(S, P) + S * 2 * sizeof(FastRow); }
-__host__ __device__ inline size_t off_jobs(int S, int P) { return off_bar(S, P) + 2 * S * 8; }  // JobP [kCW]
-__host__ __device__ inline size_t total(int S, int P) { return off_jobs(S, P) + kCW * 48; }
+__host__ __device__ inline size_t off_jobs(int S, int P) { return off_bar(S, P) + 2 * S * 8; }  // JobP [kMaxCW]
+__host__ __device__ inline size_t total(int S, int P) { return off_jobs(S, P) + kMaxCW * 48; }
 
 struct JobP {  // a compute warp's job fields, parked in shared memory
   float* zmip;
@@ -56,15 +64,16 @@ static_assert(sizeof(JobP) == 48, "JobP layout");
 // Plane of column t of a tile row, relative to the tile's first column, for
 // pixel/step = p/q at phase ph.
 __host__ __device__ constexpr int pofs(int p, int q, int ph, int t) { return per_ofs(p, q, ph, t); }
-// Column t is the first or the last of its plane interval within the tile.
-__host__ __device__ constexpr bool pcand(int p, int q, int ph, int t) {
-  return t == 0 || t == kTileJ - 1 || pofs(p, q, ph, t) != pofs(p, q, ph, t - 1) ||
+// Column t is the first or the last of its plane interval within a run of
+// `run` columns.
+__host__ __device__ constexpr bool pcand(int p, int q, int ph, int t, int run) {
+  return t == 0 || t == run - 1 || pofs(p, q, ph, t) != pofs(p, q, ph, t - 1) ||
          pofs(p, q, ph, t + 1) != pofs(p, q, ph, t);
 }
 // Number of y-max candidates before column t.
-__host__ __device__ constexpr int pcount(int p, int q, int ph, int t) {
+__host__ __device__ constexpr int pcount(int p, int q, int ph, int t, int run) {
   int n = 0;
-  for (int i = 0; i < t; ++i) n += pcand(p, q, ph, i) ? 1 : 0;
+  for (int i = 0; i < t; ++i) n += pcand(p, q, ph, i, run) ? 1 : 0;
   return n;
 }
 
@@ -79,7 +88,7 @@ struct PerRing {
   __device__ __forceinline__ uint64_t* full() const {
     return reinterpret_cast<uint64_t*>(base + per::off_bar(S, Pl));
   }
-  // consumers -> producer: slot read by both compute warps
+  // consumers -> producer: slot read by every compute warp
   __device__ __forceinline__ uint64_t* sfree() const { return full() + S; }
   __device__ __forceinline__ per::JobP* jobs() const {
     return reinterpret_cast<per::JobP*>(base + per::off_jobs(S, Pl));
@@ -95,11 +104,11 @@ __device__ __forceinline__ PerRing per_ring(unsigned char* smem, int S, int Pl) 
 }
 
 // Whole CTA: barrier init, then a CTA barrier.
-__device__ __forceinline__ void per_ring_init(const PerRing& r) {
+__device__ __forceinline__ void per_ring_init(const PerRing& r, int ncw) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < r.S; ++s) {
       mbar_init(&r.full()[s], 1);
-      mbar_init(&r.sfree()[s], per::kCW);
+      mbar_init(&r.sfree()[s], ncw);
     }
     fence_barrier_init();
   }
@@ -157,13 +166,13 @@ __device__ __forceinline__ f2 lds_x2(const unsigned char* smem, uint32_t off) {
   return u16x2_to_f2(*reinterpret_cast<const uint32_t*>(smem + off));
 }
 
-// Both camera rows of a stage for one compute warp: the tile's 32 columns,
+// Both camera rows of a stage for one compute warp: a run of RUN columns,
 // row 0 at phase PH0 and row 1 at phase PH1.  off0 / off1: shared-memory
 // offset of this lane's 2 columns x in the tile's first plane of each row;
 // wof0 / wof1: the tile's (w, w) weight pairs of each row.
-template <int Pp, int Qq, int PH0, int PH1>
+template <int RUN, int Pp, int Qq, int PH0, int PH1>
 __device__ __forceinline__ void per_pair(const unsigned char* __restrict__ smem, uint32_t off0, uint32_t off1,
-                                         uint32_t wof0, uint32_t wof1, float (&zmax)[kTileJ][per::kXL],
+                                         uint32_t wof0, uint32_t wof1, float (&zmax)[RUN][per::kXL],
                                          float (&ym0)[per::kXL], float (&ym1)[per::kXL]) {
   using namespace per;
   constexpr uint32_t pitch = kX * 2;
@@ -173,7 +182,7 @@ __device__ __forceinline__ void per_pair(const unsigned char* __restrict__ smem,
   float p0[kXL], p1[kXL];
   ulonglong2 wq0, wq1;
 #pragma unroll
-  for (int t = 0; t < kTileJ; ++t) {
+  for (int t = 0; t < RUN; ++t) {
     // next plane of a row: integers below 2^24, so the new lower plane is
     // exactly the old upper one
     if (t > 0 && pofs(Pp, Qq, PH0, t) != pofs(Pp, Qq, PH0, t - 1)) {
@@ -195,8 +204,8 @@ __device__ __forceinline__ void per_pair(const unsigned char* __restrict__ smem,
     upk(fma2((t & 1) ? wq1.y : wq1.x, d1, a1), v1[0], v1[1]);
 #pragma unroll
     for (int c = 0; c < kXL; ++c) zmax[t][c] = max3(zmax[t][c], v0[c], v1[c]);
-    if (pcand(Pp, Qq, PH0, t)) {
-      if (pcount(Pp, Qq, PH0, t) % 2 == 0) {
+    if (pcand(Pp, Qq, PH0, t, RUN)) {
+      if (pcount(Pp, Qq, PH0, t, RUN) % 2 == 0) {
 #pragma unroll
         for (int c = 0; c < kXL; ++c) p0[c] = v0[c];
       } else {
@@ -204,8 +213,8 @@ __device__ __forceinline__ void per_pair(const unsigned char* __restrict__ smem,
         for (int c = 0; c < kXL; ++c) ym0[c] = max3(ym0[c], p0[c], v0[c]);
       }
     }
-    if (pcand(Pp, Qq, PH1, t)) {
-      if (pcount(Pp, Qq, PH1, t) % 2 == 0) {
+    if (pcand(Pp, Qq, PH1, t, RUN)) {
+      if (pcount(Pp, Qq, PH1, t, RUN) % 2 == 0) {
 #pragma unroll
         for (int c = 0; c < kXL; ++c) p1[c] = v1[c];
       } else {
@@ -214,50 +223,52 @@ __device__ __forceinline__ void per_pair(const unsigned char* __restrict__ smem,
       }
     }
   }
-  if (pcount(Pp, Qq, PH0, kTileJ) % 2 == 1) {
+  if (pcount(Pp, Qq, PH0, RUN, RUN) % 2 == 1) {
 #pragma unroll
     for (int c = 0; c < kXL; ++c) ym0[c] = fmaxf(ym0[c], p0[c]);
   }
-  if (pcount(Pp, Qq, PH1, kTileJ) % 2 == 1) {
+  if (pcount(Pp, Qq, PH1, RUN, RUN) % 2 == 1) {
 #pragma unroll
     for (int c = 0; c < kXL; ++c) ym1[c] = fmaxf(ym1[c], p1[c]);
   }
 }
 
 // Phase pair idx = PH0 * Qq + PH1 in [LO, HI), by a balanced branch tree.
-template <int Pp, int Qq, int LO, int HI>
+template <int RUN, int Pp, int Qq, int LO, int HI>
 __device__ __forceinline__ void per_tree(int idx, const unsigned char* __restrict__ smem, uint32_t off0,
-                                         uint32_t off1, uint32_t wof0, uint32_t wof1,
-                                         float (&zmax)[kTileJ][per::kXL], float (&ym0)[per::kXL],
-                                         float (&ym1)[per::kXL]) {
+                                         uint32_t off1, uint32_t wof0, uint32_t wof1, float (&zmax)[RUN][per::kXL],
+                                         float (&ym0)[per::kXL], float (&ym1)[per::kXL]) {
   if constexpr (HI - LO == 1) {
-    per_pair<Pp, Qq, LO / Qq, LO % Qq>(smem, off0, off1, wof0, wof1, zmax, ym0, ym1);
+    per_pair<RUN, Pp, Qq, LO / Qq, LO % Qq>(smem, off0, off1, wof0, wof1, zmax, ym0, ym1);
   } else {
     constexpr int MID = (LO + HI) / 2;
     if (idx < MID)
-      per_tree<Pp, Qq, LO, MID>(idx, smem, off0, off1, wof0, wof1, zmax, ym0, ym1);
+      per_tree<RUN, Pp, Qq, LO, MID>(idx, smem, off0, off1, wof0, wof1, zmax, ym0, ym1);
     else
-      per_tree<Pp, Qq, MID, HI>(idx, smem, off0, off1, wof0, wof1, zmax, ym0, ym1);
+      per_tree<RUN, Pp, Qq, MID, HI>(idx, smem, off0, off1, wof0, wof1, zmax, ym0, ym1);
   }
 }
 
 // The phase of each 8-column chunk (its first column's position within the
-// period) is kept in bits 16..23 of its step word; the tile's is chunk 0's.
+// period) is kept in bits 16..23 of its step word; a run's is that of its
+// first chunk.
 constexpr int kPhaseShift = 16;
 
-// Compute warp h: all 32 columns of the job's tile for columns x
-// xbase + 64 h .. + 63, both rows of every stage.  z-maxima stay in
-// registers and are folded into zmip at the end of the job; each row's
-// y-max over the tile goes to ymip right away.  Returns false when a
-// bounded wait gave up.
-template <int Pp, int Qq>
-__device__ __forceinline__ bool per_consume(const FastJob& jb, const PerRing& r, int& g, unsigned* err, int h,
+// Compute warp i: run h = i % kRuns of the job's tile (columns
+// j0 + RUN h .. + RUN - 1) for columns x xbase + 64 (i / kRuns) .. + 63,
+// both rows of every stage.  z-maxima stay in registers and are folded into
+// zmip at the end of the job; each row's y-max over the run goes to ymip
+// right away.  Returns false when a bounded wait gave up.
+template <int RUN, int Pp, int Qq>
+__device__ __forceinline__ bool per_consume(const FastJob& jb, const PerRing& r, int& g, unsigned* err, int i,
                                             int lane) {
   using namespace per;
+  constexpr int kRuns = Cfg<RUN>::kRuns;
+  const int h = i % kRuns, xh = i / kRuns;
   const uint32_t pitch = kX * 2;
   const int S = r.S;
   const unsigned char* smem = r.base;
-  JobP* js = r.jobs() + h;
+  JobP* js = r.jobs() + i;
   if (lane == 0) {
     js->zmip = jb.zmip;
     js->ymip = jb.ymip;
@@ -269,13 +280,13 @@ __device__ __forceinline__ bool per_consume(const FastJob& jb, const PerRing& r,
     js->gend = g + (jb.ke - jb.ks + 1) / 2;
   }
   __syncwarp();
-  float zmax[kTileJ][kXL];
+  float zmax[RUN][kXL];
 #pragma unroll
-  for (int t = 0; t < kTileJ; ++t)
+  for (int t = 0; t < RUN; ++t)
 #pragma unroll
     for (int c = 0; c < kXL; ++c) zmax[t][c] = 0.0f;  // uint16 voxels are >= 0
   bool ok = true;
-  const uint32_t xoff = (uint32_t)(h * kXW + lane * kXL) * 2;  // this lane's bytes within a staged plane
+  const uint32_t xoff = (uint32_t)(xh * kXW + lane * kXL) * 2;  // this lane's bytes within a staged plane
 
 #pragma unroll 1
   for (; g < lds_volatile_s32(&js->gend); ++g) {
@@ -285,7 +296,7 @@ __device__ __forceinline__ bool per_consume(const FastJob& jb, const PerRing& r,
       break;
     }
     const uint32_t tab0 = (uint32_t)(per::off_tab(S, r.Pl) + (size_t)(s * 2) * sizeof(FastRow));
-    const uint32_t rec = (uint32_t)offsetof(FastRow, rec);
+    const uint32_t rec = (uint32_t)(offsetof(FastRow, rec) + (h * RUN / 8) * sizeof(FastRec));
     const uint2 rr0 = *reinterpret_cast<const uint2*>(smem + tab0 + rec);
     const uint2 rr1 = *reinterpret_cast<const uint2*>(smem + tab0 + (uint32_t)sizeof(FastRow) + rec);
     const int c0 = (int)((rr0.x >> kPhaseShift) & 255u);
@@ -295,15 +306,16 @@ __device__ __forceinline__ bool per_consume(const FastJob& jb, const PerRing& r,
     float ym0[kXL], ym1[kXL];
 #pragma unroll
     for (int c = 0; c < kXL; ++c) ym0[c] = ym1[c] = 0.0f;
-    per_tree<Pp, Qq, 0, Qq * Qq>(c0 * Qq + c1, smem, row0 + rr0.y * pitch, row1 + rr1.y * pitch, tab0,
-                                 tab0 + (uint32_t)sizeof(FastRow), zmax, ym0, ym1);
+    const uint32_t wof0 = tab0 + (uint32_t)(h * RUN * 8);
+    per_tree<RUN, Pp, Qq, 0, Qq * Qq>(c0 * Qq + c1, smem, row0 + rr0.y * pitch, row1 + rr1.y * pitch, wof0,
+                                      wof0 + (uint32_t)sizeof(FastRow), zmax, ym0, ym1);
     __syncwarp();
     if (lane == 0) mbar_arrive(&r.sfree()[s]);
     float* ymip = lds_volatile_ptr(&js->ymip);
     if (ymip) {
       const int nx = lds_volatile_s32(&js->nx);
       const int k0 = lds_volatile_s32(&js->k0g) + 2 * g;
-      const int x = lds_volatile_s32(&js->xbase) + h * kXW + lane * kXL;
+      const int x = lds_volatile_s32(&js->xbase) + xh * kXW + lane * kXL;
       const bool second = k0 + 1 < lds_volatile_s32(&js->nz);
 #pragma unroll
       for (int c = 0; c < kXL; ++c) {
@@ -318,10 +330,10 @@ __device__ __forceinline__ bool per_consume(const FastJob& jb, const PerRing& r,
   float* zmip = lds_volatile_ptr(&js->zmip);
   if (zmip) {
     const int nx = lds_volatile_s32(&js->nx);
-    const int x = lds_volatile_s32(&js->xbase) + h * kXW + lane * kXL;
-    const int j0 = lds_volatile_s32(&js->j0);
+    const int x = lds_volatile_s32(&js->xbase) + xh * kXW + lane * kXL;
+    const int j0 = lds_volatile_s32(&js->j0) + h * RUN;
 #pragma unroll
-    for (int t = 0; t < kTileJ; ++t) {
+    for (int t = 0; t < RUN; ++t) {
       float* row = zmip + (size_t)(j0 + t) * nx;
 #pragma unroll
       for (int c = 0; c < kXL; ++c)

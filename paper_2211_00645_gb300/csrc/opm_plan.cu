@@ -249,10 +249,7 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
           const int ph = phase(fr, fp, fq);
           for (int g = 0; g < 4; ++g) fr.rec[g].adv |= (unsigned)((8 * g * fp + ph) % fq) << 16;
         }
-        const char* pv = std::getenv("OPM_PER_VARIANT");
-        p->per_variant = pv ? std::atoi(pv) & 3 : 0;
-        static const int lps[4] = {4, 6, 5, 5};
-        p->lists_per_sm = lps[p->per_variant];
+        p->lists_per_sm = kPerCtasPerSm;
       }
     }
 
@@ -390,6 +387,15 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
   v.linear = interp == OPM_INTERP_LINEAR;
   v.rinv = (float)(step / pixel);
   *out = p;
+  return OPM_OK;
+}
+
+opm_status opm_plan_path(const opm_plan* p, int* path, int* fam_p, int* fam_q) {
+  if (!p) return fail(OPM_ERR_INVALID_ARG, "plan is NULL");
+  const bool fast = p->fast_ok && !p->force_generic;
+  if (path) *path = !fast ? OPM_PATH_GENERAL : p->family ? OPM_PATH_PERIODIC : OPM_PATH_FAST;
+  if (fam_p) *fam_p = (fast && p->family) ? kFamilies[p->family - 1].p : 0;
+  if (fam_q) *fam_q = (fast && p->family) ? kFamilies[p->family - 1].q : 0;
   return OPM_OK;
 }
 

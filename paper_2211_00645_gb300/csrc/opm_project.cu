@@ -110,13 +110,13 @@ k_project_fast(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
 // Periodic kernel (opm_periodic.cuh): the fast kernel's schedule, tables
 // and TMA ring for plans with pixel/step = Pp/Qq, with straight-line compute
 // warps per phase pair; MINB CTAs per SM, S ring stages.
-template <int Pp, int Qq, int MINB, int S>
-__global__ void __launch_bounds__(per::kThreads, MINB)
+template <int Pp, int Qq, int RUN, int MINB, int S>
+__global__ void __launch_bounds__(per::Cfg<RUN>::kThreads, MINB)
 k_project_per(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
   const PlanView& v = args.v;
   extern __shared__ __align__(128) unsigned char smem[];
   const PerRing ring = per_ring(smem, S, args.P);
-  per_ring_init(ring);
+  per_ring_init(ring, per::Cfg<RUN>::kCW);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   int g = 0;
@@ -151,7 +151,7 @@ k_project_per(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
     if (warp == 0)
       ok = per_produce(jb, ring, g, v.err, lane);
     else
-      ok = per_consume<Pp, Qq>(jb, ring, g, v.err, warp - 1, lane);
+      ok = per_consume<RUN, Pp, Qq>(jb, ring, g, v.err, warp - 1, lane);
   }
   if (warp == 0) per_drain(ring, g, ok, v.err);
 }
@@ -535,26 +535,15 @@ opm_status launch_per_f(const opm_plan* p, const CUtensorMap& map, const ProjArg
   if constexpr (F < kNumFamilies) {
     if (p->family - 1 != F) return launch_per_f<F + 1>(p, map, args, s, grid_div);
     constexpr int Pp = kFamilies[F].p, Qq = kFamilies[F].q;
-    static int done[4][64] = {{0}};
-    const int pv = p->per_variant & 3;
-    opm_status st = pv == 0   ? prepare_kernel(k_project_per<Pp, Qq, 4, 6>, p->device, done[0])
-                    : pv == 1 ? prepare_kernel(k_project_per<Pp, Qq, 6, 4>, p->device, done[1])
-                    : pv == 2 ? prepare_kernel(k_project_per<Pp, Qq, 5, 5>, p->device, done[2])
-                              : prepare_kernel(k_project_per<Pp, Qq, 5, 4>, p->device, done[3]);
+    static int done[64] = {0};
+    opm_status st = prepare_kernel(k_project_per<Pp, Qq, kPerRun, kPerCtasPerSm, kPerStages>, p->device, done);
     if (st != OPM_OK) return st;
     const PlanView& v = p->view;
     const int full = std::min(v.nunits, v.nlists);
     if (full == 0) return OPM_OK;
     const int grid = std::max(1, full / std::max(1, grid_div));
-    const int P = args.P;
-    if (pv == 0)
-      k_project_per<Pp, Qq, 4, 6><<<grid, per::kThreads, per::total(6, P), s>>>(map, args);
-    else if (pv == 1)
-      k_project_per<Pp, Qq, 6, 4><<<grid, per::kThreads, per::total(4, P), s>>>(map, args);
-    else if (pv == 2)
-      k_project_per<Pp, Qq, 5, 5><<<grid, per::kThreads, per::total(5, P), s>>>(map, args);
-    else
-      k_project_per<Pp, Qq, 5, 4><<<grid, per::kThreads, per::total(4, P), s>>>(map, args);
+    k_project_per<Pp, Qq, kPerRun, kPerCtasPerSm, kPerStages>
+        <<<grid, per::Cfg<kPerRun>::kThreads, per::total(kPerStages, args.P), s>>>(map, args);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_project_per");
   } else {
@@ -612,7 +601,7 @@ opm_status launch_project(const opm_plan* p, const void* raw, opm_dtype in_t, fl
                       ((size_t)v.ncols * es) % 16 == 0 && P <= 256;
   const bool gen_ok = tma_ok && (int)(u16 ? gen::total<uint16_t>(P) : gen::total<float>(P)) <= smax;
   const bool fast = gen_ok && u16 && !zsum && !argz && p->fast_ok && v.frow &&
-                    (int)(p->family ? per::total(6, P) : fast::total(P)) <= smax;
+                    (int)(p->family ? per::total(kPerStages, P) : fast::total(P)) <= smax;
 
   if (!gen_ok) {
     const long long nzx = (long long)v.ny * v.nx, nyx = (long long)v.nz * v.nx;

@@ -118,3 +118,17 @@ def test_shape_arguments_optional(opm):
     nz = ctypes.c_int64()
     assert opm.load().opm_plan_shape(p.handle, ctypes.byref(nz), None, None, None) == opm.OPM_OK
     assert nz.value == 6
+
+
+def test_plan_path_classification(opm):
+    """Which live-view kernel a plan takes is decided on the host: pixel/step
+    = 1/3 plans take the periodic kernel, other pixel <= step plans the fast
+    one, pixel > step plans the general one."""
+    cases = [((200, 512, 2048, 35.0, 0.3, 0.1), (opm.OPM_PATH_PERIODIC, 1, 3)),
+             ((33, 50, 200, 60.0, 0.45, 0.15), (opm.OPM_PATH_PERIODIC, 1, 3)),
+             ((64, 128, 128, 30.0, 0.4, 0.115), (opm.OPM_PATH_FAST, 0, 0)),
+             ((16, 20, 64, 35.0, 0.05, 0.1), (opm.OPM_PATH_GENERAL, 0, 0))]
+    for shape, want in cases:
+        plan = opm.Plan(*shape)
+        assert opm.opm_plan_path(plan) == want, shape
+        plan.close()

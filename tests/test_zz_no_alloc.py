@@ -106,3 +106,59 @@ def test_limits_are_enforced(lib):
     lib.batch_project_static(items, check=True)
     _equal(items, ref)
     assert np.isfinite(items[0]["zmip"].cpu().numpy()).all()
+
+
+def test_capture_is_refused(lib):
+    """The call copies a process-wide host image with a pageable copy, which a
+    graph cannot record: on a capturing stream it refuses and launches
+    nothing, and the stream stays usable."""
+    items = _items(lib, 500)
+    ref = _reference(lib, items)
+    lib.batch_project_static(items, check=True)          # set-up happens outside the capture
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            with pytest.raises(lib.OpmError) as e:
+                lib.batch_project_static(items, stream=s)
+        finally:
+            g.capture_end()
+    assert e.value.status == lib.OPM_ERR_UNSUPPORTED and "captured" in str(e.value)
+    for it in items:
+        for k in ("zmip", "ymip"):
+            if it[k] is not None:
+                it[k].fill_(-4.0)
+    lib.batch_project_static(items, stream=s)
+    s.synchronize()
+    _equal(items, ref)
+
+
+def test_threads_on_one_stream(lib):
+    """Two host threads call it at once on one stream: the shared host image
+    is built and copied under a lock, and the kernels run in stream order, so
+    each thread's results equal the allocating path's."""
+    import threading
+    sets = [_items(lib, 600), _items(lib, 700)]
+    refs = [_reference(lib, it) for it in sets]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    errors = []
+
+    def worker(items):
+        try:
+            for _ in range(20):
+                lib.batch_project_static(items, stream=s)
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    ts = [threading.Thread(target=worker, args=(it,)) for it in sets]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    s.synchronize()
+    assert not errors, errors
+    for items, ref in zip(sets, refs):
+        _equal(items, ref)

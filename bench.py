@@ -1,13 +1,13 @@
 """Benchmark of the OPM deskew library on the live-view stack.
 
-Workload (one step): the 200 scan planes x 512 rows x 2048 columns uint16
-stack (theta 35 deg, step 0.3 um, pixel 0.1 um, Poisson(100) + 2000 blobs):
-  1. the fused live view: deskew + z-MIP + y-MIP, no volume in memory;
-  2. the full FP32 deskewed volume (512 x 1021 x 2048);
-both from one opm_deskew_mip call, whose two kernels run side by side.  Each
-kernel is also timed alone, for the per-kernel table and the roofline.
-Metric: deskew GB/s of algorithmic bytes (raw read once + every output written
-once), with the fraction of the measured HBM copy bandwidth, and volumes/s.
+Workload (one step): the fused live view of the 200 scan planes x 512 rows x
+2048 columns uint16 stack (theta 35 deg, step 0.3 um, pixel 0.1 um,
+Poisson(100) + 2000 blobs): deskew + z-MIP + y-MIP in one opm_project call,
+with no volume in memory.  Metric: deskew GB/s of algorithmic bytes (raw read
+once + both projections written once), its fraction of the measured HBM copy
+bandwidth, and volumes/s.  The separate full FP32 volume run of the same
+stack (alone, beside the live view, and as one fused kernel) is reported
+under "volume"; the other workloads under their own keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -36,12 +36,14 @@ import numpy as np  # noqa: E402
 import opm_synth  # noqa: E402
 
 WORKLOAD = "liveview_200x512x2048"
-METRIC = "deskew GB/s (fused live view + FP32 volume, algorithmic bytes)"
+METRIC = "deskew GB/s (fused deskew + z-MIP + y-MIP live view, algorithmic bytes)"
 UNIT = "GB/s"
 
 # Sources each timed kernel is compiled from: a change to any of them voids
 # the stored ncu traffic figure.
 KERNEL_SOURCES = {
+    "periodic": ["csrc/opm_project.cu", "csrc/opm_periodic.cuh", "csrc/opm_tma.cuh", "csrc/opm_common.cuh",
+                 "csrc/opm_internal.h", "csrc/opm_sched.h", "csrc/opm_plan.cu", "../include/opm.h"],
     "liveview": ["csrc/opm_project.cu", "csrc/opm_tma.cuh", "csrc/opm_common.cuh", "csrc/opm_internal.h",
                  "csrc/opm_sched.h", "csrc/opm_plan.cu", "../include/opm.h"],
     "volume_f32": ["csrc/opm_deskew.cu", "csrc/opm_common.cuh", "csrc/opm_internal.h", "csrc/opm_sched.h",
@@ -156,7 +158,6 @@ def run_reference(args):
     Rc = Rfull[:, :, :cal].astype(np.float64)
     t0 = time.perf_counter()
     O.project(Rc, gc)
-    O.deskew(Rc, gc)
     t_col = (time.perf_counter() - t0) / cal
     ncol = int(args.ref_budget_s / ((args.steps + args.warmup) * t_col))
     ncol = max(8, min(args.ref_cols, ncol))
@@ -164,18 +165,16 @@ def run_reference(args):
     g = O.geometry(cfg.nscan, cfg.nrows, ncol, cfg.theta_deg, cfg.step, cfg.pixel)
     sub = opm_synth.StackConfig("r", cfg.nscan, cfg.nrows, ncol, cfg.theta_deg, cfg.step, cfg.pixel,
                                 0, (1, 1), (1, 1))
-    live, vol = algorithmic_bytes(sub, g.ny)
+    live, _ = algorithmic_bytes(sub, g.ny)
     for _ in range(args.warmup):
         O.project(R, g)
-        O.deskew(R, g)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         O.project(R, g)
-        O.deskew(R, g)
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
-    value = (live + vol) / t / 1e9
+    value = live / t / 1e9
     sample = f"first {ncol} of {cfg.ncols} x-columns of the {WORKLOAD} stack (x-columns are independent)"
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
@@ -194,13 +193,12 @@ def cpu_baseline(R, cfg, cols, budget_s=20.0):
     g = O.geometry(cfg.nscan, cfg.nrows, cols, cfg.theta_deg, cfg.step, cfg.pixel)
     sub = opm_synth.StackConfig("s", cfg.nscan, cfg.nrows, cols, cfg.theta_deg, cfg.step, cfg.pixel,
                                 0, (1, 1), (1, 1))
-    live, vol = algorithmic_bytes(sub, g.ny)
+    live, _ = algorithmic_bytes(sub, g.ny)
     t0 = time.perf_counter()
     O.project(Rs, g)
-    O.deskew(Rs, g)
     t = time.perf_counter() - t0
-    return {"value": round((live + vol) / t / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {cols} of {cfg.ncols} x-columns (project + deskew, {t:.1f} s)"}
+    return {"value": round(live / t / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {cols} of {cfg.ncols} x-columns (z-MIP + y-MIP of the oracle's volume, {t:.1f} s)"}
 
 
 def _oracle_chunk(job):
@@ -210,7 +208,6 @@ def _oracle_chunk(job):
     g = O.geometry(*geo)
     t0 = time.perf_counter()
     O.project(R, g)
-    O.deskew(R, g)
     return time.perf_counter() - t0
 
 
@@ -227,14 +224,14 @@ def cpu_baseline_all_cores(R, cfg, cols=None):
     sub = opm_synth.StackConfig("a", cfg.nscan, cfg.nrows, cols, cfg.theta_deg, cfg.step, cfg.pixel,
                                 0, (1, 1), (1, 1))
     import oracle as O
-    live, vol = algorithmic_bytes(sub, O.geometry(cfg.nscan, cfg.nrows, cols, cfg.theta_deg, cfg.step,
-                                                  cfg.pixel).ny)
+    live, _ = algorithmic_bytes(sub, O.geometry(cfg.nscan, cfg.nrows, cols, cfg.theta_deg, cfg.step,
+                                                cfg.pixel).ny)
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
         pool.map(_oracle_chunk, [(j[0][:, :, :1], j[1][:2] + (1,) + j[1][3:]) for j in jobs])  # start-up
         t0 = time.perf_counter()
         pool.map(_oracle_chunk, jobs)
         t = time.perf_counter() - t0
-    return {"value": round((live + vol) / t / 1e9, 4), "unit": UNIT, "cores": len(jobs), "kind": "oracle",
+    return {"value": round(live / t / 1e9, 4), "unit": UNIT, "cores": len(jobs), "kind": "oracle",
             "sample": f"first {cols} of {cfg.ncols} x-columns in {len(jobs)} processes ({t:.1f} s)"}
 
 
@@ -527,32 +524,23 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        # live view and FP32 volume in one call: the two kernels run side by side
-        opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+        # the live view: deskew + z-MIP + y-MIP in one call, no volume in memory
+        opm.opm_project(plan, raw, zmip, None, ymip, None, stream)
 
     for _ in range(args.warmup):
         step()
-        opm.opm_project(plan, raw, zmip, None, ymip, None, stream)
         opm.opm_deskew(plan, raw, vol, stream)
+        opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
     torch.cuda.synchronize()
     opm.opm_plan_check(plan)
 
-    # ---- device-resident timing: per-kernel events on the launching stream
+    # ---- device-resident timing of the step (CUDA events on the launching stream)
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     sampler = ClockSampler(torch.cuda.current_device())
     if rank == 0:
         sampler.start()
     pdist.barrier()
     torch.cuda.synchronize()
-    # (1) each kernel alone, one after the other: per-kernel times and roofline
-    for i in range(K):
-        ev[i][0].record(stream)
-        opm.opm_project(plan, raw, zmip, None, ymip, None, stream)
-        ev[i][1].record(stream)
-        opm.opm_deskew(plan, raw, vol, stream)
-        ev[i][2].record(stream)
-    # (2) the step: both outputs from one opm_deskew_mip call
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
@@ -562,14 +550,29 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop() if rank == 0 else None
     total_ms = t_start.elapsed_time(t_end)
-    t_live = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(K)) * 1e-3
-    t_vol = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(K)) * 1e-3
-    serial_ms = ev[0][0].elapsed_time(ev[K - 1][2]) / K
     ms_step = pdist.max_over_ranks(total_ms / K, device=dev)
     opm.opm_plan_check(plan)
 
+    # ---- the separate full FP32 volume run of the same stack: the volume alone,
+    # and volume + live view from one opm_deskew_mip call (side by side)
+    KV = max(20, K // 8)
+    v0, v1, v2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    v0.record(stream)
+    for _ in range(KV):
+        opm.opm_deskew(plan, raw, vol, stream)
+    v1.record(stream)
+    for _ in range(KV):
+        opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+    v2.record(stream)
+    torch.cuda.synchronize()
+    t_vol = v0.elapsed_time(v1) / KV * 1e-3
+    t_pair = v1.elapsed_time(v2) / KV * 1e-3
+    opm.opm_plan_check(plan)
+    opm.opm_plan_check(plan)
+
     # ---- end to end through the C ABI: every step copies its stack in from
-    # pinned host memory and its live view back out.  Two device stack
+    # pinned host memory and both projections back out (the bytes of the
+    # metric are the live view's: raw in, z-MIP and y-MIP out).  Two device stack
     # buffers: the copy of step i + 1 (copy stream) overlaps the compute of
     # step i (compute stream).
     E = max(10, K // 10)
@@ -579,7 +582,7 @@ def main():
     freed = [torch.cuda.Event() for _ in range(2)]
 
     def step_on(r):
-        opm.opm_deskew_mip(plan, r, vol, None, zmip, ymip, stream)
+        opm.opm_project(plan, r, zmip, None, ymip, None, stream)
 
     # two untimed pipelined steps first: the copy stream's first use
     for b in range(2):
@@ -618,44 +621,48 @@ def main():
         return
 
     peak, peak_src = peaks()
-    step_bytes = live_b + vol_b
-    value = ws * step_bytes / (ms_step * 1e-3) / 1e9
-    kernels = {
-        "liveview": {"bytes": live_b, "us": round(t_live * 1e6, 2), "GBps": round(live_b / t_live / 1e9, 1),
-                     "frac": round(live_b / t_live / 1e9 / peak, 4), "launches_per_step": 2,
-                     "volumes_per_s": round(1.0 / t_live, 1)},
-        "volume_f32": {"bytes": vol_b, "us": round(t_vol * 1e6, 2), "GBps": round(vol_b / t_vol / 1e9, 1),
-                       "frac": round(vol_b / t_vol / 1e9 / peak, 4), "launches_per_step": 1},
-    }
-    dom = max(kernels, key=lambda k: kernels[k]["us"])
-    tr = NCU_TRAFFIC.get(dom)
-    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(dom) else None
-    ach = kernels[dom]["GBps"]
+    value = ws * live_b / (ms_step * 1e-3) / 1e9
+    path = opm.opm_plan_path(plan)
+    kname = {opm.OPM_PATH_PERIODIC: "periodic", opm.OPM_PATH_FAST: "liveview"}.get(path[0], "liveview_general")
+    tr = NCU_TRAFFIC.get(kname)
+    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(kname) else None
+    ach = live_b / (ms_step * 1e-3) / 1e9
+    pair_b = live_b + vol_b
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u16->f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "raw": [cfg.nscan, cfg.nrows, cfg.ncols], "theta_deg": cfg.theta_deg,
                    "step_um": cfg.step, "pixel_um": cfg.pixel, "grid": [plan.nz, plan.ny, plan.nx],
-                   "step": "fused z-MIP+y-MIP live view and full FP32 volume, one opm_deskew_mip call "
-                           "(the two kernels side by side)",
-                   "l2": "inputs larger than L2 (raw 419 MB, volume 4.28 GB)",
+                   "step": "fused deskew + z-MIP + y-MIP live view, one opm_project call, no volume in memory",
+                   "kernel_path": {"path": kname, "pixel_over_step": f"{path[1]}/{path[2]}" if path[1] else None},
+                   "l2": "input larger than L2 (raw 419 MB)",
                    "parallelism": f"{ws} independent stacks" if ws > 1 else "1 GPU"},
         "volumes_per_s": round(ws / (ms_step * 1e-3), 2),
-        "liveview_volumes_per_s": kernels["liveview"]["volumes_per_s"],
-        "kernels": kernels,
-        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                     "frac": round(ach / peak, 4), "traffic": traffic, "kernel": dom,
+        "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "traffic": traffic,
+                     "kernel": f"k_project_{'per' if kname == 'periodic' else 'fast'} + k_init_outputs "
+                               "(one opm_project call, timed together)",
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
-        "e2e": {"value": round(ws * step_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
+        "e2e": {"value": round(ws * live_b / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(host_raw.numel() * 2),
                 "d2h_bytes_per_step": int((host_z.numel() + host_y.numel()) * 4),
                 "ms_per_step": round(e2e_ms, 4)},
-        "gpu_launches": 3 * K,
+        "gpu_launches": 2 * K,
         "host": {"cores": os.cpu_count(), "library_sources_sha": _tree_sha()},
         "clocks": clocks,
     }
-    line["serial_ms_per_step"] = round(serial_ms, 4)   # the two kernels one after the other
+    vtr = NCU_TRAFFIC.get("volume_f32")
+    line["volume"] = {
+        "what": "the separate full FP32 volume run of the same stack (512 x 1021 x 2048)",
+        "deskew_f32": {"bytes": vol_b, "us": round(t_vol * 1e6, 2), "GBps": round(vol_b / t_vol / 1e9, 1),
+                       "frac": round(vol_b / t_vol / 1e9 / peak, 4), "volumes_per_s": round(1.0 / t_vol, 1),
+                       "traffic": vtr["bytes_per_launch"] if vtr and vtr["src_sha"] == _src_sha("volume_f32") else None},
+        "deskew_mip_side_by_side": {"call": "opm_deskew_mip (volume + live view, the two kernels side by side)",
+                                    "bytes": pair_b, "us": round(t_pair * 1e6, 2),
+                                    "GBps": round(pair_b / t_pair / 1e9, 1),
+                                    "frac": round(pair_b / t_pair / 1e9 / peak, 4)},
+    }
     # the same outputs from the single fused kernel (raw read once)
     os.environ["OPM_ONE_PASS_FUSED"] = "1"
     try:
@@ -674,7 +681,7 @@ def main():
     t_one = f0.elapsed_time(f1) / 20 * 1e-3
     del plan_f
     one_b = vol_b + live_b - 2 * cfg.nscan * cfg.nrows * cfg.ncols
-    line["one_pass"] = {"call": "opm_deskew_mip, single fused kernel (plan made with OPM_ONE_PASS_FUSED=1)",
+    line["volume"]["one_pass_fused"] = {"call": "opm_deskew_mip, single fused kernel (plan made with OPM_ONE_PASS_FUSED=1)",
                         "bytes": one_b, "us": round(t_one * 1e6, 2), "GBps": round(one_b / t_one / 1e9, 1),
                         "frac": round(one_b / t_one / 1e9 / peak, 4)}
     # the paper's own sheet-frame view (shear of Eq. 1) and a shear-warp view

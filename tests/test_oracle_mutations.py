@@ -44,6 +44,9 @@ def _pins_pass():
     # extent
     g = O.geometry(200, 512, 4, 35.0, 0.3, 0.1)
     ok &= (g.J0, g.ny) == (2, 1021)
+    # fully covered region, counted by hand (n_f = j - k/2)
+    g = O.geometry(3, 2, 1, 60.0, 0.125, 0.125)
+    ok &= np.array_equal(O.covered_mask(g), np.array([[1, 1, 1, 0], [0, 1, 1, 0]], dtype=bool))
     return bool(ok)
 
 
@@ -104,6 +107,16 @@ def _mip_backward_next_row(gz, argz, g):
     return G
 
 
+def _covered_strict(g):
+    nf = M.plane_coord(g, np.arange(g.ny)[None, :], np.arange(g.nz)[:, None])
+    return (nf > 0.0) & (nf < g.nscan - 1)
+
+
+def _covered_wide(g):
+    nf = M.plane_coord(g, np.arange(g.ny)[None, :], np.arange(g.nz)[:, None])
+    return (nf > -1.0) & (nf < g.nscan)
+
+
 _real_mip_backward = M.mip_backward
 
 
@@ -120,6 +133,8 @@ def _mip_backward_clipped_rows(gz, argz, g):
     ("skew_adjoint", _shifted_adjoint),
     ("mip_backward", _mip_backward_next_row),
     ("mip_backward", _mip_backward_clipped_rows),
+    ("covered_mask", _covered_strict),
+    ("covered_mask", _covered_wide),
 ])
 def test_pins_catch_mutant(monkeypatch, target, mutant):
     monkeypatch.setattr(M, target, mutant)

@@ -77,6 +77,27 @@ def test_constant_reproduced_on_covered_region(p):
     np.testing.assert_allclose(V[cov], 1234.0, rtol=0, atol=1e-9)
 
 
+def test_covered_mask_hand_counted():
+    """The fully covered region {0 <= n_f <= nscan - 1}, counted by hand on
+    geometries whose n_f is exact in binary: the constant and affine pins use
+    this mask, so it must be neither too wide nor too narrow."""
+    # theta 60 (cos = 1/2), step = pixel: n_f = j - k/2, J0 = 0, ny = ceil(3 + 1/2) = 4
+    g = O.geometry(3, 2, 1, 60.0, 0.125, 0.125)
+    assert (g.J0, g.ny) == (0, 4)
+    want = np.array([[1, 1, 1, 0],    # n_f = 0, 1, 2, 3
+                     [0, 1, 1, 0]],   # n_f = -1/2, 1/2, 3/2, 5/2
+                    dtype=bool)
+    assert np.array_equal(O.covered_mask(g), want)
+    # step = 2 pixel: n_f = (j - 1)/2 - k/4, J0 = 1, ny = ceil(1 + 6 + 1) = 8
+    g = O.geometry(3, 3, 1, 60.0, 0.25, 0.125)
+    assert (g.J0, g.ny) == (1, 8)
+    want = np.zeros((3, 8), dtype=bool)
+    want[0, 1:6] = True               # (j - 1)/2 in [0, 2]
+    want[1, 2:6] = True               # (j - 1)/2 - 1/4 in [0, 2]: j - 1 in [1/2, 9/2]
+    want[2, 2:7] = True               # (j - 1)/2 - 1/2 in [0, 2]: j - 1 in [1, 5]
+    assert np.array_equal(O.covered_mask(g), want)
+
+
 @pytest.mark.parametrize("p", TINY + [(64, 128, 4, 30.0, 0.4, 0.115)])
 def test_affine_ramp_reproduced(p):
     """R = a n + b r + c x + d  ->  V = a n_f + b k + c x + d where fully covered."""

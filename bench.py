@@ -472,6 +472,54 @@ def serve_bench(args, torch):
     return out
 
 
+def one_pass(torch, opm, cfg, raw, vol, zmip, ymip, stream, vol_b, live_b, peak):
+    """The FP32 volume and the live view from the single fused kernel (raw
+    read once): a plan made with OPM_ONE_PASS_FUSED=1."""
+    os.environ["OPM_ONE_PASS_FUSED"] = "1"
+    try:
+        plan_f = opm.Plan(cfg.nscan, cfg.nrows, cfg.ncols, cfg.theta_deg, cfg.step, cfg.pixel)
+    finally:
+        os.environ.pop("OPM_ONE_PASS_FUSED", None)
+    for _ in range(3):
+        opm.opm_deskew_mip(plan_f, raw, vol, None, zmip, ymip, stream)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(20):
+        opm.opm_deskew_mip(plan_f, raw, vol, None, zmip, ymip, stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t_one = f0.elapsed_time(f1) / 20 * 1e-3
+    del plan_f
+    one_b = vol_b + live_b - 2 * cfg.nscan * cfg.nrows * cfg.ncols
+    return {"call": "opm_deskew_mip, single fused kernel (plan made with OPM_ONE_PASS_FUSED=1)",
+            "bytes": one_b, "us": round(t_one * 1e6, 2), "GBps": round(one_b / t_one / 1e9, 1),
+            "frac": round(one_b / t_one / 1e9 / peak, 4)}
+
+
+def sheet_bench(torch, opm, cfg, raw, stream, peak):
+    """The paper's own sheet-frame view (the shear of Eq. 1) of the stack."""
+    import math as _m
+    shear = cfg.step * _m.cos(_m.radians(cfg.theta_deg)) / cfg.pixel
+    sheet = opm.opm_sheet_project(raw, shear, stream=stream)
+    for _ in range(3):
+        opm.opm_sheet_project(raw, shear, out=sheet, stream=stream)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(20):
+        opm.opm_sheet_project(raw, shear, out=sheet, stream=stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    t_sheet = s0.elapsed_time(s1) / 20 * 1e-3
+    sheet_b = 2 * cfg.nscan * cfg.nrows * cfg.ncols + 4 * sheet.numel()
+    out = {"call": "opm_sheet_project", "shear_rows_per_frame": round(shear, 6),
+           "out": list(sheet.shape), "bytes": sheet_b, "us": round(t_sheet * 1e6, 2),
+           "GBps": round(sheet_b / t_sheet / 1e9, 1), "frac": round(sheet_b / t_sheet / 1e9 / peak, 4)}
+    del sheet
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,7 +535,16 @@ def main():
     ap.add_argument("--serve-saturated", type=int, default=1800, help="stacks arriving at once (0: skip)")
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-ring-gb", type=int, default=8)
+    ap.add_argument("--nscan", type=int, default=0,
+                    help="scan planes of the live-view stack (0: the workload's 200; smaller for profiler captures)")
+    ap.add_argument("--only", default="all",
+                    help="comma list of the sections run after the live-view step: volume, sheet, "
+                         "differentiable, rolling, large, serving, cpu (or all, none)")
     args = ap.parse_args()
+    sections = {"volume", "sheet", "differentiable", "rolling", "large", "serving", "cpu"}
+    only = sections if args.only == "all" else set() if args.only == "none" else set(args.only.split(","))
+    if only - sections:
+        ap.error(f"unknown sections {sorted(only - sections)}")
     if args.warmup < 3:
         args.warmup = 3
 
@@ -509,6 +566,9 @@ def main():
     opm.load()
 
     cfg = opm_synth.CONFIGS[WORKLOAD]
+    if args.nscan:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, nscan=args.nscan)
     R = opm_synth.raw_stack(cfg)
     plan = opm.Plan(cfg.nscan, cfg.nrows, cfg.ncols, cfg.theta_deg, cfg.step, cfg.pixel)
     live_b, vol_b = algorithmic_bytes(cfg, plan.ny)
@@ -555,7 +615,7 @@ def main():
 
     # ---- the separate full FP32 volume run of the same stack: the volume alone,
     # and volume + live view from one opm_deskew_mip call (side by side)
-    KV = max(20, K // 8)
+    KV = max(20, K // 8) if "volume" in only else 1
     v0, v1, v2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     v0.record(stream)
     for _ in range(KV):
@@ -632,7 +692,8 @@ def main():
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u16->f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "raw": [cfg.nscan, cfg.nrows, cfg.ncols], "theta_deg": cfg.theta_deg,
+        "config": {"workload": WORKLOAD if not args.nscan else f"{WORKLOAD} with {cfg.nscan} scan planes",
+                   "raw": [cfg.nscan, cfg.nrows, cfg.ncols], "theta_deg": cfg.theta_deg,
                    "step_um": cfg.step, "pixel_um": cfg.pixel, "grid": [plan.nz, plan.ny, plan.nx],
                    "step": "fused deskew + z-MIP + y-MIP live view, one opm_project call, no volume in memory",
                    "kernel_path": {"path": kname, "pixel_over_step": f"{path[1]}/{path[2]}" if path[1] else None},
@@ -663,55 +724,24 @@ def main():
                                     "GBps": round(pair_b / t_pair / 1e9, 1),
                                     "frac": round(pair_b / t_pair / 1e9 / peak, 4)},
     }
-    # the same outputs from the single fused kernel (raw read once)
-    os.environ["OPM_ONE_PASS_FUSED"] = "1"
-    try:
-        plan_f = opm.Plan(cfg.nscan, cfg.nrows, cfg.ncols, cfg.theta_deg, cfg.step, cfg.pixel)
-    finally:
-        os.environ.pop("OPM_ONE_PASS_FUSED", None)
-    for _ in range(3):
-        opm.opm_deskew_mip(plan_f, raw, vol, None, zmip, ymip, stream)
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(20):
-        opm.opm_deskew_mip(plan_f, raw, vol, None, zmip, ymip, stream)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    t_one = f0.elapsed_time(f1) / 20 * 1e-3
-    del plan_f
-    one_b = vol_b + live_b - 2 * cfg.nscan * cfg.nrows * cfg.ncols
-    line["volume"]["one_pass_fused"] = {"call": "opm_deskew_mip, single fused kernel (plan made with OPM_ONE_PASS_FUSED=1)",
-                        "bytes": one_b, "us": round(t_one * 1e6, 2), "GBps": round(one_b / t_one / 1e9, 1),
-                        "frac": round(one_b / t_one / 1e9 / peak, 4)}
-    # the paper's own sheet-frame view (shear of Eq. 1) and a shear-warp view
-    import math as _m
-    shear = cfg.step * _m.cos(_m.radians(cfg.theta_deg)) / cfg.pixel
-    sheet = opm.opm_sheet_project(raw, shear, stream=stream)
-    for _ in range(3):
-        opm.opm_sheet_project(raw, shear, out=sheet, stream=stream)
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(20):
-        opm.opm_sheet_project(raw, shear, out=sheet, stream=stream)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    t_sheet = s0.elapsed_time(s1) / 20 * 1e-3
-    sheet_b = 2 * cfg.nscan * cfg.nrows * cfg.ncols + 4 * sheet.numel()
-    line["sheet_view"] = {"call": "opm_sheet_project", "shear_rows_per_frame": round(shear, 6),
-                          "out": list(sheet.shape), "bytes": sheet_b, "us": round(t_sheet * 1e6, 2),
-                          "GBps": round(sheet_b / t_sheet / 1e9, 1), "frac": round(sheet_b / t_sheet / 1e9 / peak, 4)}
-    del sheet
-    line["differentiable"] = adjoint_bench(torch, opm, peak)
-    line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
-    if not args.no_large:
+    if "volume" not in only:
+        del line["volume"]
+    else:
+        line["volume"]["one_pass_fused"] = one_pass(torch, opm, cfg, raw, vol, zmip, ymip, stream, vol_b, live_b,
+                                                    peak)
+    if "sheet" in only:
+        line["sheet_view"] = sheet_bench(torch, opm, cfg, raw, stream, peak)
+    if "differentiable" in only:
+        line["differentiable"] = adjoint_bench(torch, opm, peak)
+    if "rolling" in only:
+        line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
+    if "large" in only and not args.no_large:
         line["large_volume"] = large_bench(torch, opm, peak)
-    if args.serve_paced > 0 or args.serve_saturated > 0:
+    if "serving" in only:
         del vol, raw
         torch.cuda.empty_cache()
         line["serving"] = serve_bench(args, torch)
-    if not args.no_cpu_baseline:
+    if "cpu" in only and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(R, cfg, args.ref_cols)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(R, cfg)
     print(json.dumps(line), flush=True)

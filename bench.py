@@ -435,12 +435,16 @@ def serve_bench(args, torch):
     link0 = link_gbs()
     out = {"workload": "serving: ROIs rows {256,512,1024} x cols {512,1024,2048}, planes 50..400, 2 channels, "
                        "theta 35, step 0.3, pixel 0.1; z-MIP + y-MIP per channel",
-           "budget_bytes": budget, "ring_bytes": ring.nbytes}
+           "budget_bytes": budget, "ring_bytes": ring.nbytes,
+           "camera": f"paced: each stack acquired frame by frame at {args.serve_fps:g} frames/s, complete at its "
+                     "Poisson time; the batched server copies frames as they are written, the plain server "
+                     "copies the complete stack; saturated: every stack complete at once",
+           "latency": "stack complete (last frame written) -> both views of every channel in host memory"}
     phases = [("paced", args.serve_rate, args.serve_paced), ("saturated", None, args.serve_saturated)]
 
-    def one(make, rate, n, seed):
+    def one(make, rate, n, seed, fps=None, stream=False):
         srv = make()
-        cam = Camera(srv, ring, shapes, n, rate, seed=seed)
+        cam = Camera(srv, ring, shapes, n, rate, seed=seed, fps=fps, stream_frames=stream)
         cam.start()
         srv.run(cam.expected(), timeout_s=600)
         cam.join(timeout=60)
@@ -464,7 +468,9 @@ def serve_bench(args, torch):
         for phase, rate, n in phases:
             if n > 0:
                 ring.stalls = 0
-                out.setdefault(phase, {"rate_per_s": rate, "stacks": n})[name] = one(make, rate, n, seed=2)
+                fps = args.serve_fps if rate else None
+                out.setdefault(phase, {"rate_per_s": rate, "stacks": n})[name] = one(
+                    make, rate, n, seed=2, fps=fps, stream=(name == "batched" and fps is not None))
     link1 = link_gbs()
     out["h2d_link_gbs"] = {"before": link0, "after": link1}
     out["mean_raw_bytes"] = round(mean_raw)
@@ -535,6 +541,7 @@ def main():
     ap.add_argument("--serve-saturated", type=int, default=1800, help="stacks arriving at once (0: skip)")
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-ring-gb", type=int, default=8)
+    ap.add_argument("--serve-fps", type=float, default=2000.0, help="camera frame rate of the paced phase")
     ap.add_argument("--nscan", type=int, default=0,
                     help="scan planes of the live-view stack (0: the workload's 200; smaller for profiler captures)")
     ap.add_argument("--only", default="all",

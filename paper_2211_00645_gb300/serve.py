@@ -154,6 +154,25 @@ class PinnedRing:
             self.peak = max(self.peak, sum(e[1] for e in self._entries))
             return off
 
+    def try_acquire(self, nbytes: int, refs: int = 1) -> Optional[int]:
+        """``acquire`` that returns None at once instead of waiting (no stall
+        is counted: the caller decides what a failed attempt means)."""
+        size = self._round(max(1, nbytes))
+        if size > self.nbytes:
+            raise ValueError(f"stack of {nbytes} bytes exceeds the {self.nbytes}-byte ring")
+        with self._cond:
+            off = self._place(size)
+            if off is None:
+                return None
+            self._entries.append([off, size, int(refs)])
+            self.peak = max(self.peak, sum(e[1] for e in self._entries))
+            return off
+
+    def wait_release(self, timeout: float) -> None:
+        """Sleeps until a range is returned or ``timeout`` seconds pass."""
+        with self._cond:
+            self._cond.wait(max(0.0, timeout))
+
     def release(self, off: int) -> None:
         with self._cond:
             for e in self._entries:
@@ -206,6 +225,16 @@ class Request:
     res_arena: Optional["DeviceArena"] = None  # pinned arena holding ``results``
     res_off: int = -1
     geometry: Optional[Tuple[float, float, float]] = None  # (theta, step, pixel) it was served with
+    # device clock of its copy in (perf_counter seconds): when the copy engine
+    # started it (after any earlier copy on the stream) and when it landed
+    t_h2d_start: float = 0.0
+    t_h2d_end: float = 0.0
+    # planes written by the camera so far (a stack is complete at nscan)
+    frames_ready: int = -1
+
+    def __post_init__(self):
+        if self.frames_ready < 0:
+            self.frames_ready = self.nscan
 
     def release_host(self) -> None:
         if self.ring is not None:
@@ -319,7 +348,9 @@ class _Resident:
             ny = 4 * plan.nz * plan.nx
             self.y.append(arena.view(pos, ny).view(torch.float32).view(plan.nz, plan.nx))
             pos += (ny + 255) // 256 * 256
-        self.h2d = None
+        self.h2d = None           # event after the latest copy in
+        self.h2d_start = None     # event before the copy of the last planes
+        self.copied = 0           # planes whose copy has been issued
         self.launched = False
 
 
@@ -359,6 +390,15 @@ class LiveViewServer:
         self.peak_in_use = 0
         self.ticks = 0
         self.batch_sizes: List[int] = []
+        # a timed event on the copy stream and its host time: converts the
+        # copies' device timestamps to the host clock of the latencies
+        self._clock_ev = None
+        self._clock_host = 0.0
+        # copy scheduling: pieces of a stack and the bytes kept queued
+        self.copy_piece = 64 << 20
+        self.copy_backlog = 512 << 20
+        self._h2d_q: deque = deque()   # (event after a copy, its bytes), oldest first
+        self._h2d_inflight = 0
 
     @property
     def plans(self) -> PlanCache:
@@ -417,13 +457,73 @@ class LiveViewServer:
                     break
                 self.waiting.popleft()
                 r = _Resident(req, plan, off, self.arena, torch)
-                with torch.cuda.stream(self.h2d):
-                    r.raw.view(torch.int16).copy_(req.host.view(torch.int16), non_blocking=True)
-                    r.h2d = torch.cuda.Event()
-                    r.h2d.record(self.h2d)
+                if self._clock_ev is None:
+                    self._calibrate_clock()
                 req.t_admit = time.perf_counter()
                 self.resident.append(r)
                 self.peak_in_use = max(self.peak_in_use, self.arena.in_use)
+
+    def _calibrate_clock(self) -> None:
+        """Host time of a timed event on the copy stream.  The host reads its
+        clock after the event completes, so each reading is late by the
+        synchronisation delay; the smallest of a few readings is kept."""
+        torch = self.torch
+        self._clock_ev = torch.cuda.Event(enable_timing=True)
+        self._clock_ev.record(self.h2d)
+        self._clock_ev.synchronize()
+        best = time.perf_counter()
+        for _ in range(4):
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(self.h2d)
+            ev.synchronize()
+            best = min(best, time.perf_counter() - self._clock_ev.elapsed_time(ev) * 1e-3)
+        self._clock_host = best
+
+    def _copy_frames(self, r: "_Resident", max_bytes: int) -> int:
+        """Issues the copy of the next planes the camera has written for this
+        request, at most ``max_bytes`` (at least one plane); returns bytes."""
+        torch = self.torch
+        plane = 2 * r.plan.nrows * r.plan.ncols * r.req.channels
+        a = r.copied
+        b = min(r.req.frames_ready, r.plan.nscan, a + max(1, max_bytes // plane))
+        if b <= a:
+            return 0
+        host = r.req.host.view(torch.int16)
+        with torch.cuda.stream(self.h2d):
+            if b == r.plan.nscan:
+                r.h2d_start = torch.cuda.Event(enable_timing=True)
+                r.h2d_start.record(self.h2d)
+            r.raw.view(torch.int16)[a:b].copy_(host[a:b], non_blocking=True)
+            r.h2d = torch.cuda.Event(enable_timing=True)
+            r.h2d.record(self.h2d)
+        r.copied = b
+        nbytes = (b - a) * plane
+        self._h2d_q.append((r.h2d, nbytes))
+        return nbytes
+
+    def _copy_more(self) -> None:
+        """Copies frames that have arrived for admitted requests, in pieces
+        of at most ``copy_piece`` bytes, keeping at most ``copy_backlog``
+        bytes queued on the copy stream: complete stacks first (their
+        latency is running), oldest first, then stacks still being
+        acquired.  A stack that has just been completed thus waits for at
+        most the backlog, not for other stacks' whole copies."""
+        q = self._h2d_q
+        while q and q[0][0].query():
+            self._h2d_inflight -= q.popleft()[1]
+        pend = [r for r in self.resident if r.copied < r.plan.nscan and r.req.frames_ready > r.copied]
+        if not pend:
+            return
+        pend.sort(key=lambda r: (r.req.frames_ready < r.plan.nscan, r.req.t_arrival))
+        while self._h2d_inflight < self.copy_backlog and pend:
+            r = pend[0]
+            n = self._copy_frames(r, self.copy_piece)
+            self._h2d_inflight += n
+            if r.copied >= min(r.req.frames_ready, r.plan.nscan):
+                pend.pop(0)
+
+    def _landed(self, r: "_Resident") -> bool:
+        return r.copied == r.plan.nscan and r.h2d.query()
 
     def _launch_tick(self) -> bool:
         torch = self.torch
@@ -433,7 +533,7 @@ class LiveViewServer:
         nitems = 0
         full = False
         for r in self.resident:
-            if r.launched or not r.h2d.query():
+            if r.launched or not self._landed(r):
                 continue
             r.req.release_host()                 # copy landed: the ring range is free
             if full or nitems + r.req.channels > self.max_items:
@@ -494,6 +594,8 @@ class LiveViewServer:
         self.inflight.popleft()
         for r in ready:
             r.req.t_done = t
+            r.req.t_h2d_start = self._clock_host + self._clock_ev.elapsed_time(r.h2d_start) * 1e-3
+            r.req.t_h2d_end = self._clock_host + self._clock_ev.elapsed_time(r.h2d) * 1e-3
             if not self.keep_results:
                 r.req.release_results()
             self.arena.free(r.off)
@@ -507,21 +609,23 @@ class LiveViewServer:
         nvtx = self.torch.cuda.nvtx
         nvtx.range_push("opm.admit")
         self._admit()
+        self._copy_more()
         nvtx.range_pop()
         nvtx.range_push("opm.launch_tick")
         launched = self._launch_tick()
         nvtx.range_pop()
         retired = self._retire(block=False)
-        if not launched and not retired and self.inflight:
+        if not launched and not retired and (self.inflight or self.resident):
             # nothing to launch or retire yet: hand landed copies' ring ranges
             # back to the camera and poll again shortly (a blocking wait on
-            # the oldest tick would hold them and stall the camera)
+            # the oldest tick would hold them and stall the camera; a busy
+            # loop would starve the camera thread)
             self._release_landed()
             time.sleep(self.poll_s)
 
     def _release_landed(self) -> None:
         for r in self.resident:
-            if not r.launched and r.req.ring is not None and r.h2d.query():
+            if not r.launched and r.req.ring is not None and self._landed(r):
                 r.req.release_host()
 
     def run(self, n_expected: int, timeout_s: float = 600.0, idle=None) -> None:
@@ -617,26 +721,44 @@ class PlainServer:
 
 
 class Camera(threading.Thread):
-    """Camera stand-in: writes stacks into a pinned ring and publishes them at
-    Poisson arrival times.
+    """Camera stand-in: writes stacks into a pinned ring and publishes them.
 
     ``shapes`` lists request shapes (nscan, nrows, ncols per channel,
-    channels); arrival i takes ``shapes[order[i]]`` with a seeded order.
-    ``rate`` stacks/s (None: all at once, saturating).  A request's arrival
-    time is its scheduled time, so a stall on a full ring counts as lag.
+    channels); stack i takes ``shapes[order[i]]`` with a seeded order and is
+    complete at a Poisson time (``rate`` stacks/s; None: all at once,
+    saturating).  A request's arrival time is that completion time, so a
+    stall on a full ring counts as lag.
+
+    ``fps``: frames per second of the acquisition.  With it, stack i is
+    acquired plane by plane over the nscan / fps seconds that end at its
+    completion time: its ring range is taken when its first frame is due
+    and ``frames_ready`` grows as its frames are written (in steps of
+    ``chunk_frames``).  ``stream_frames`` submits the request with its first
+    frames, so a server can copy frames while the stack is still being
+    acquired (the paper builds the projection as each image is received);
+    otherwise the request is submitted complete.  Without ``fps`` every
+    stack is written at once at its completion time.
+
     Host-side fault injection for tests: ``drop`` (arrival indices never
     delivered), ``duplicate`` (delivered twice, sharing one ring range) and
     ``delay_s`` (extra delay per index).
     """
 
     def __init__(self, server, ring: PinnedRing, shapes, n: int, rate: Optional[float], seed: int = 0,
-                 drop=(), duplicate=(), delay_s=None, ring_timeout: float = 120.0):
+                 drop=(), duplicate=(), delay_s=None, ring_timeout: float = 120.0, fps: Optional[float] = None,
+                 stream_frames: bool = False, chunk_frames: int = 8):
         super().__init__(daemon=True)
         self.server, self.ring, self.shapes, self.n, self.rate = server, ring, list(shapes), n, rate
         rng = np.random.default_rng(seed)
         self.order = rng.integers(0, len(self.shapes), n)
         gaps = rng.exponential(1.0 / rate, n) if rate else np.zeros(n)
         self.offsets = np.cumsum(gaps) - (gaps[0] if n else 0.0)
+        self.fps = float(fps) if fps else None
+        if self.fps:   # the first stack's first frame is due at the start
+            lead = max(self.shapes[int(k)][0] for k in self.order) / self.fps if n else 0.0
+            self.offsets = self.offsets + lead
+        self.stream_frames = bool(stream_frames) and self.fps is not None
+        self.chunk_frames = max(1, int(chunk_frames))
         self.drop, self.duplicate = set(drop), set(duplicate)
         self.delay_s = dict(delay_s or {})
         self.ring_timeout = ring_timeout
@@ -653,28 +775,100 @@ class Camera(threading.Thread):
         except BaseException as e:        # surfaced by the caller through ``error``
             self.error = e
 
+    def _wait_until(self, t: float) -> None:
+        while True:
+            now = time.perf_counter()
+            if now >= t:
+                return
+            time.sleep(min(t - now, 0.001))
+
     def _run(self) -> None:
+        import heapq
         self.t0 = time.perf_counter()
         rid = 0
+        # stack starts (first frame due) in time order, taken strictly one
+        # after the other; frame updates and completions of the stacks being
+        # acquired, in time order
+        starts, updates = [], []
+        seq = 0
         for i in range(self.n):
-            t = self.t0 + self.offsets[i] + self.delay_s.get(i, 0.0)
-            while True:
-                now = time.perf_counter()
-                if now >= t:
-                    break
-                time.sleep(min(t - now, 0.001))
             if i in self.drop:
                 continue
-            nscan, nrows, ncols, C = self.shapes[int(self.order[i])]
-            shape = (nscan, nrows, ncols * C)
-            copies = 2 if i in self.duplicate else 1
-            off = self.ring.acquire(2 * nscan * nrows * ncols * C, refs=copies, timeout=self.ring_timeout)
-            host = self.ring.view(off, shape)
-            for _ in range(copies):
-                self.server.submit(Request(rid, nscan, nrows, ncols, C, host, t_arrival=t, ring=self.ring,
-                                           ring_off=off))
-                rid += 1
-                self.delivered += 1
+            t_done = self.t0 + self.offsets[i] + self.delay_s.get(i, 0.0)
+            nscan = self.shapes[int(self.order[i])][0]
+            heapq.heappush(starts, (t_done - nscan / self.fps if self.fps else t_done, seq, i))
+            seq += 1
+        live = {}   # index -> [requests, time of the first frame, completion time, nscan, frames written]
+        t_refused = None  # when the ring first refused the next stack
+        while starts or updates:
+            now = time.perf_counter()
+            if starts and starts[0][0] <= now and (not updates or starts[0][0] <= updates[0][0]):
+                t, _, i = starts[0]
+                nscan, nrows, ncols, C = self.shapes[int(self.order[i])]
+                copies = 2 if i in self.duplicate else 1
+                off = self.ring.try_acquire(2 * nscan * nrows * ncols * C, refs=copies)
+                if off is None:
+                    # ring full: this stack (and every later one) waits and its
+                    # lag grows, while the stacks being acquired keep writing
+                    if t_refused is None:
+                        t_refused = now
+                        self.ring.stalls += 1
+                    elif now - t_refused > self.ring_timeout:
+                        raise TimeoutError("pinned ring full")
+                    if not (updates and updates[0][0] <= now):
+                        nxt = updates[0][0] - now if updates else 0.05
+                        self.ring.wait_release(min(max(nxt, 0.0), 0.05))
+                        continue
+                    off = -1                   # due frame updates first
+            else:
+                off = -1
+            if off >= 0:
+                heapq.heappop(starts)
+                if t_refused is not None:      # acquisition starts late: frames are due from now
+                    t, t_refused = max(t, now), None
+                host = self.ring.view(off, (nscan, nrows, ncols * C))
+                t_done = self.t0 + self.offsets[i] + self.delay_s.get(i, 0.0)
+                reqs = []
+                for _ in range(copies):
+                    reqs.append(Request(rid, nscan, nrows, ncols, C, host, t_arrival=t_done, ring=self.ring,
+                                        ring_off=off, frames_ready=0 if self.fps else nscan))
+                    rid += 1
+                live[i] = [reqs, t, t_done, nscan, 0]
+                if self.stream_frames:
+                    for r in reqs:
+                        self.server.submit(r)
+                        self.delivered += 1
+                heapq.heappush(updates, ((t if self.fps else t_done), seq, 1 if self.fps else 2, i))
+                seq += 1
+                continue
+            if updates and updates[0][0] <= now:
+                _, _, kind, i = heapq.heappop(updates)
+                if kind == 1:                  # frames written so far, in whole chunks
+                    reqs, t_first, t_done, nscan, written = live[i]
+                    due = min(nscan, int((now - t_first) * self.fps))
+                    if due < nscan:
+                        due = due // self.chunk_frames * self.chunk_frames
+                    if due > written:
+                        live[i][4] = due
+                        for r in reqs:
+                            r.frames_ready = due
+                    if due < nscan:
+                        t_next = t_first + min(nscan, due + self.chunk_frames) / self.fps
+                        heapq.heappush(updates, (t_next, seq, 1, i))
+                    else:
+                        heapq.heappush(updates, (t_done, seq, 2, i))
+                    seq += 1
+                else:                          # stack complete
+                    reqs = live.pop(i)[0]
+                    for r in reqs:
+                        r.frames_ready = r.nscan
+                    if not self.stream_frames:
+                        for r in reqs:
+                            self.server.submit(r)
+                            self.delivered += 1
+                continue
+            nxt = min([q[0][0] for q in (starts, updates) if q])
+            self._wait_until(nxt)
 
 
 def serve_stats(server, t_first: float) -> dict:
@@ -686,12 +880,19 @@ def serve_stats(server, t_first: float) -> dict:
     t_last = max((r.t_done for r in done), default=t_first)
     span = max(t_last - t_first, 1e-9)
     ch = sum(r.channels for r in done)
-    parts = {"queue": [(r.t_admit - r.t_arrival) * 1e3 for r in done],
-             "copy_in": [(r.t_launch - r.t_admit) * 1e3 for r in done],
+    # a request streamed frame by frame is admitted before its stack is
+    # complete: its queueing is then zero and its copy-in runs from arrival
+    parts = {"queue": [max(0.0, r.t_admit - r.t_arrival) * 1e3 for r in done],
+             "copy_in": [(r.t_launch - max(r.t_admit, r.t_arrival)) * 1e3 for r in done],
              "finish": [(r.t_done - r.t_launch) * 1e3 for r in done]}
     out = {"served": len(done), "rejected": len(server.rejected),
            "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99), "max_ms": max(lat) if lat else None,
            "stacks_per_s": len(done) / span, "volumes_per_s": ch / span, "span_s": span}
+    timed = [r for r in done if r.t_h2d_end > 0.0]
+    if timed:   # device clock of the copies: queued behind earlier copies, then copying
+        parts["h2d_wait"] = [(r.t_h2d_start - max(r.t_admit, r.t_arrival)) * 1e3 for r in timed]
+        parts["h2d_copy"] = [(r.t_h2d_end - r.t_h2d_start) * 1e3 for r in timed]
+        parts["h2d_landed_to_launch"] = [(r.t_launch - r.t_h2d_end) * 1e3 for r in timed]
     for k, v in parts.items():
         out[f"{k}_p50_ms"] = percentile(v, 50)
         out[f"{k}_p99_ms"] = percentile(v, 99)

@@ -177,7 +177,11 @@ def test_geometry_change_while_serving(ring):
 
     for i, shp in enumerate(SHAPES):
         submit(i, shp)
-    srv.step()                                    # admits (and may launch) the first five
+    for _ in range(20000):                        # admit the first five until their copies land
+        srv.step()
+        if all(r.ring is None for r in reqs):     # ring ranges returned
+            break
+    assert all(r.ring is None for r in reqs)
     srv.set_geometry(45.0, 0.2, 0.115)
     for i, shp in enumerate(SHAPES):
         submit(10 + i, shp)
@@ -187,4 +191,17 @@ def test_geometry_change_while_serving(ring):
     geos = {r.rid: r.geometry for r in srv.done}
     assert all(geos[i] == GEOM for i in range(5))
     assert all(geos[10 + i] == (45.0, 0.2, 0.115) for i in range(5))
+    _check_results(srv.done)
+
+
+def test_streamed_frames_equal_plain_path(ring):
+    """Frames copied to the device as the camera writes them (the projection
+    runs once the stack is complete): every result equals the plain path,
+    and requests were admitted while their stacks were still being
+    acquired."""
+    srv, cam = _run(ring, 24, budget=256 << 20, rate=300.0, fps=20000.0, stream_frames=True, chunk_frames=8,
+                    drop={5}, duplicate={9})
+    assert len(srv.done) == cam.expected() == 24
+    assert sum(r.t_admit < r.t_arrival for r in srv.done) >= len(srv.done) // 2
+    assert all(r.t_done > r.t_arrival for r in srv.done)
     _check_results(srv.done)

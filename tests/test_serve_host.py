@@ -149,3 +149,62 @@ def test_camera_stall_counts_as_lag():
 def test_percentile_helper():
     assert percentile([], 50) is None
     assert percentile([1.0, 2.0, 3.0], 50) == 2.0
+
+
+def test_camera_streams_frames_before_completion():
+    """With a frame rate and streaming on, a request is published with its
+    first frames, well before its stack is complete; its ready-frame count
+    only grows, in whole chunks, and reaches nscan at the arrival time."""
+    import threading
+    shapes = [(40, 8, 8, 2), (24, 8, 8, 1)]
+    ring = _ring(1 << 16)
+    got, seen = [], []
+
+    class Rec:
+        def submit(self, req):
+            got.append((time.perf_counter(), req.frames_ready, req))
+
+    cam = Camera(Rec(), ring, shapes, n=6, rate=50.0, seed=2, fps=2000.0, stream_frames=True, chunk_frames=8)
+    stop = threading.Event()
+
+    def watch():
+        while not stop.is_set():
+            for _, _, r in list(got):
+                seen.append((r.rid, r.nscan, r.frames_ready))
+            time.sleep(0.0002)
+
+    w = threading.Thread(target=watch)
+    w.start()
+    cam.start()
+    cam.join(timeout=30)
+    stop.set()
+    w.join()
+    assert cam.error is None and len(got) == 6
+    for t_sub, fr0, r in got:
+        assert fr0 == 0 and t_sub < r.t_arrival - 0.5 * r.nscan / 2000.0
+        assert r.frames_ready == r.nscan
+        r.release_host()
+    last = {}
+    for rid, nscan, f in seen:
+        assert f >= last.get(rid, 0)
+        last[rid] = f
+        assert f == nscan or f % 8 == 0
+    assert max(last.values()) > 0 and ring.in_use() == 0
+
+
+def test_camera_frame_rate_without_streaming_submits_complete_stacks():
+    shapes = [(30, 8, 8, 2)]
+    ring = _ring(1 << 16)
+    got = []
+
+    class Rec:
+        def submit(self, req):
+            got.append((time.perf_counter(), req.frames_ready, req))
+            req.release_host()
+
+    cam = Camera(Rec(), ring, shapes, n=4, rate=100.0, seed=3, fps=3000.0)
+    cam.start()
+    cam.join(timeout=30)
+    assert cam.error is None and len(got) == 4
+    for t_sub, fr, r in got:
+        assert fr == r.nscan and t_sub >= r.t_arrival

@@ -412,6 +412,7 @@ def serve_bench(args, torch):
     ``serve_rate`` stacks/s, then with every stack arriving at once."""
     from paper_2211_00645_gb300.serve import Camera, LiveViewServer, PinnedRing, PlainServer, PlanCache, \
         serve_stats
+    from paper_2211_00645_gb300.tune import SHAPE_IDS
     shapes = opm_synth.serve_shapes(256, seed=11)
     plans = PlanCache(35.0, 0.3, 0.1)
     for (n, r, c, _) in set(shapes):
@@ -461,7 +462,8 @@ def serve_bench(args, torch):
     out["tuned"] = tuned
     mean_raw = sum(2 * n * r * c * C for (n, r, c, C) in shapes) / len(shapes)
     makers = {"batched": lambda: LiveViewServer(plans, budget, keep_results=False, kchunk=tuned["kchunk"],
-                                                ctas_per_sm=tuned["ctas_per_sm"]),
+                                                ctas_per_sm=tuned["ctas_per_sm"],
+                                                shape=SHAPE_IDS[tuned["shape"]]),
               "plain": lambda: PlainServer(plans, keep_results=False)}
     for name, make in makers.items():
         one(make, None, 16, seed=1)                                   # warm-up: allocators, plans

@@ -259,13 +259,20 @@ opm_status opm_mip_backward(const opm_plan* plan, const float* g_zmip,
                             void* cuda_stream);
 
 /*
- * Batched live view: one persistent launch computes the fused z-MIP / y-MIP
- * (as opm_project with U16 input) of many stacks, channels and ROIs of uneven
+ * Batched live view: persistent launches compute the projections (as
+ * opm_project with U16 input) of many stacks, channels and ROIs of uneven
  * sizes.  Multi-colour acquisitions split every camera frame into channels,
  * each deskewed on its own (the paper's channel split in the section "Methods
  * for the fast processing and visualisation of lightsheet data"); here a
  * channel is an item whose raw pointer and pitches select its ROI of a
  * shared frame stack.
+ *
+ * Items whose plan the fast kernels take (opm_plan_path: FAST or PERIODIC)
+ * and that ask for z-MIP and/or y-MIP only run in one persistent launch of
+ * the fast (or periodic) kernel over row chunks.  All other items (pixel >
+ * step, ny < 32, or a z-sum or arg-max output) run in a second persistent
+ * launch of the general kernel, one unit per tile and whole row band.
+ * Results equal opm_project's for the same plan and outputs.
  */
 typedef struct opm_batch opm_batch; /* opaque; owns device + pinned work lists */
 
@@ -276,63 +283,92 @@ typedef struct {
   int64_t plane_pitch;  /* elements between scan planes (0: nrows*row_pitch) */
   float* zmip;          /* [ny][nx] device output, or NULL                 */
   float* ymip;          /* [nz][nx] device output, or NULL                 */
+  float* zsum;          /* [ny][nx] device output, or NULL                 */
+  int32_t* argz;        /* [ny][nx] device output (first arg-max), or NULL */
 } opm_batch_item;
 
 /*
  * opm_batch_create - work lists for up to max_items items and max_units
  * (<= 2^26) work units (a unit is one 32-column j-tile x 128-column x-tile x
- * row chunk of one item; 32 bytes of work list each).  Allocates device
- * memory and pinned host memory once; the other batch calls allocate nothing
- * except the CUDA graph of opm_batch_launch_graph.
+ * row chunk of one item, or a whole row band for items of the general
+ * kernel; 32 bytes of work list each).  Allocates device memory and pinned
+ * host memory once; the other batch calls allocate nothing except the CUDA
+ * graph of opm_batch_launch_graph.
  * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_OUT_OF_MEMORY, OPM_ERR_CUDA.
  */
 opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out);
 
 /*
+ * Kernel shapes of the batch (results are bit for bit the same for every
+ * shape; only the speed differs, see the autotuner).  The shape applies to
+ * the items the fast kernels may take; the others always run in the general
+ * kernel.  The periodic shapes need every such item to share one periodic
+ * plan family (opm_plan_path: PERIODIC with the same p/q), else they fall
+ * back to OPM_SHAPE_FAST_J8X4.
+ */
+typedef enum {
+  OPM_SHAPE_AUTO = 0,      /* periodic 32 x 2 for one shared family, else fast 8 x 4     */
+  OPM_SHAPE_FAST_J8X4 = 1, /* fast kernel: 8 columns j per warp x 4 columns x per lane,  */
+                           /* two rows per stage                                          */
+  OPM_SHAPE_PER_J32X2 = 2, /* periodic kernel: 32 columns j per warp x 2 x per lane      */
+  OPM_SHAPE_PER_J16X2 = 3, /* periodic kernel: 16 columns j per warp x 2 x per lane      */
+  OPM_SHAPE_GEN_J8X4 = 4   /* general kernel for every item: 8 j x 4 x, whole row band   */
+                           /* per unit, one row per stage                                 */
+} opm_shape;
+
+/*
  * opm_batch_set - host-side preparation of the work list (TMA descriptors of
- * every item, unit list sorted by decreasing length).  kchunk = rows per
- * unit (0: 64).  Waits until the previous opm_batch_upload of this batch has
- * completed before overwriting its pinned staging.  Every item's plan must
- * have pixel <= step (consecutive output columns at most one scan plane
- * apart) and ny >= 32, and live on the batch's device; raw pointers must be
+ * every item, unit lists sorted by decreasing length).  kchunk = rows per
+ * unit of the fast kernels (0: 64); shape = an opm_shape (the one used is
+ * reported by opm_batch_info).  Waits until the previous
+ * opm_batch_upload of this batch has completed before overwriting its pinned
+ * staging.  Every item's plan must live on the batch's device and stage at
+ * most 256 planes per row (opm_project's TMA path); raw pointers must be
  * 16-byte aligned and pitches multiples of 8 elements.
  * Errors: OPM_ERR_INVALID_ARG (NULL, counts, pitches), OPM_ERR_UNSUPPORTED
- * (plan not eligible, alignment, capacity exceeded), OPM_ERR_CUDA.
+ * (slab depth, alignment, capacity exceeded), OPM_ERR_CUDA.
  */
-opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk);
+opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk, int shape);
 
 /* opm_batch_upload - asynchronous copy of the prepared work list (only its
- * used bytes: a 256-byte header, 192 bytes per item, 32 per output and 32 per
+ * used bytes: a 256-byte header, 256 bytes per item, 32 per output and 32 per
  * unit) to the device on cuda_stream.
  * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_CUDA. */
 opm_status opm_batch_upload(opm_batch* b, void* cuda_stream);
 
 /*
- * opm_batch_launch - zeroes the items' outputs and runs the persistent fused
- * projection over all units on cuda_stream (ctas_per_sm in 1..4, 0: 4).
- * The kernels take the unit and output counts from the device copy of the
- * work list, so the two launches may be captured in a CUDA graph by the
- * caller and replayed after later set + upload calls of any content with
- * the same slab depth (plans of the same theta, step and pixel) and grid.
+ * opm_batch_launch - zeroes the outputs combined by atomic max and runs the
+ * persistent projections over all units on cuda_stream (ctas_per_sm in
+ * 1..4, 0: 4; the general kernel runs at most 2 CTAs per SM).  The kernels
+ * take the unit and output counts from the device copy of the work list, so
+ * the launches may be captured in a CUDA graph by the caller and replayed
+ * after later set + upload calls of any content with the same slab depths
+ * (plans of the same theta, step and pixel), the same kinds of items (fast
+ * kernels, general kernel) and the same grid.
  * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED, OPM_ERR_CUDA.
  */
 opm_status opm_batch_launch(opm_batch* b, int ctas_per_sm, void* cuda_stream);
 
 /*
- * opm_batch_launch_graph - as opm_batch_launch, through a CUDA graph the
- * batch owns: captured on first use (on a private stream, so cuda_stream may
- * be the legacy default stream), re-captured only when the slab depth or the
- * grid changes, and launched on cuda_stream.  The graph always runs
- * ctas_per_sm x SM persistent CTAs; those without units return at once.
+ * opm_batch_launch_graph - as opm_batch_launch, through CUDA graphs the
+ * batch owns, one per launch shape (kernel shape, periodic family, slab
+ * depths, kinds of items and grids; the 4 most recently used are kept):
+ * captured on first use of a launch shape (on a private stream, so
+ * cuda_stream may be the legacy default stream) and launched on
+ * cuda_stream.  The graph always runs
+ * persistent grids (ctas_per_sm x SM CTAs of the fast kernels, up to 2 x SM
+ * of the general kernel, for the kinds of items present); CTAs without
+ * units return at once.
  * Errors: OPM_ERR_INVALID_ARG, OPM_ERR_UNSUPPORTED, OPM_ERR_CUDA.
  */
 opm_status opm_batch_launch_graph(opm_batch* b, int ctas_per_sm, void* cuda_stream);
 
-/* Items, units and shared-memory bytes of the prepared batch, and how many
- * times opm_batch_launch_graph has captured its graph (any pointer may be
- * NULL).  Errors: OPM_ERR_INVALID_ARG. */
+/* Items, work units (of both kernels), the larger of the two kernels'
+ * shared-memory bytes per CTA and the opm_shape used for the prepared batch,
+ * and how many graphs opm_batch_launch_graph has captured (any pointer may
+ * be NULL).  Errors: OPM_ERR_INVALID_ARG. */
 opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes,
-                          int* graph_captures);
+                          int* graph_captures, int* shape);
 
 /* Synchronising diagnostic, as opm_plan_check for the batch's launches. */
 opm_status opm_batch_check(const opm_batch* b);

@@ -34,7 +34,8 @@ _STATUS = {
 class opm_batch_item(ctypes.Structure):
     """Mirror of the C struct opm_batch_item."""
     _fields_ = [("plan", ctypes.c_void_p), ("raw", ctypes.c_void_p), ("row_pitch", ctypes.c_int64),
-                ("plane_pitch", ctypes.c_int64), ("zmip", ctypes.c_void_p), ("ymip", ctypes.c_void_p)]
+                ("plane_pitch", ctypes.c_int64), ("zmip", ctypes.c_void_p), ("ymip", ctypes.c_void_p),
+                ("zsum", ctypes.c_void_p), ("argz", ctypes.c_void_p)]
 
 
 # Every symbol the header declares, with its ctypes signature.
@@ -65,12 +66,13 @@ _SIGS = {
     "opm_mip_backward": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "opm_plan_check": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)]),
-    "opm_batch_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "opm_batch_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "opm_batch_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "opm_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "opm_batch_launch_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "opm_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
-                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
     "opm_batch_check": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_batch_project_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -162,6 +164,11 @@ def opm_plan_shape(plan: Plan):
 
 
 OPM_PATH_GENERAL, OPM_PATH_FAST, OPM_PATH_PERIODIC = 0, 1, 2
+
+# opm_shape: kernel shapes of the batched launch (same results, different speed)
+OPM_SHAPE_AUTO, OPM_SHAPE_FAST_J8X4, OPM_SHAPE_PER_J32X2, OPM_SHAPE_PER_J16X2, OPM_SHAPE_GEN_J8X4 = 0, 1, 2, 3, 4
+SHAPE_NAMES = {OPM_SHAPE_AUTO: "auto", OPM_SHAPE_FAST_J8X4: "fast_j8x4", OPM_SHAPE_PER_J32X2: "per_j32x2",
+               OPM_SHAPE_PER_J16X2: "per_j16x2", OPM_SHAPE_GEN_J8X4: "gen_j8x4"}
 
 
 def opm_plan_path(plan: Plan):
@@ -365,29 +372,39 @@ def mip_backward(plan: Plan, g_zmip, argz, stream=None):
 
 
 # ----------------------------------------------------------------- batches
+def _batch_items(items):
+    """C array of opm_batch_item for dicts {plan, raw, zmip?, ymip?, zsum?,
+    argz?, row_pitch?, plane_pitch?}, and the objects it points into."""
+    arr = (opm_batch_item * max(1, len(items)))()
+    keep = []
+    for i, it in enumerate(items):
+        raw = it["raw"]
+        if not raw.is_cuda:
+            raise ValueError("raw must be a CUDA tensor")
+        outs = [it.get(k) for k in ("zmip", "ymip", "zsum", "argz")]
+        ptrs = [o.data_ptr() if o is not None else None for o in outs]
+        arr[i] = opm_batch_item(it["plan"].handle.value, raw.data_ptr(), int(it.get("row_pitch", 0)),
+                                int(it.get("plane_pitch", 0)), *ptrs)
+        keep.append((it["plan"], raw, *outs))
+    return arr, keep
+
+
 def batch_project_static(items, kchunk: int = 0, ctas_per_sm: int = 0, check: bool = False, stream=None):
     """``opm_batch_project_static``: the batched live view of ``items`` (dicts
     as for ``Batch.set``) in one call that allocates no device memory, for
     callers that must not allocate (a fixed memory plan, a per-frame
     deadline).  At most 64 items and 65536 work units; calls that overlap on
     one device race."""
-    arr = (opm_batch_item * max(1, len(items)))()
-    for i, it in enumerate(items):
-        raw = it["raw"]
-        if not raw.is_cuda:
-            raise ValueError("raw must be a CUDA tensor")
-        z, y = it.get("zmip"), it.get("ymip")
-        arr[i] = opm_batch_item(it["plan"].handle.value, raw.data_ptr(), int(it.get("row_pitch", 0)),
-                                int(it.get("plane_pitch", 0)), z.data_ptr() if z is not None else None,
-                                y.data_ptr() if y is not None else None)
+    arr, _ = _batch_items(items)
     _check(load().opm_batch_project_static(ctypes.cast(arr, ctypes.c_void_p), len(items), int(kchunk),
                                            int(ctas_per_sm), int(bool(check)), _stream(stream)),
            "opm_batch_project_static")
 
 
 class Batch:
-    """Owns an ``opm_batch*``: one persistent launch of the fused z-MIP/y-MIP
-    over many uint16 stacks, channels (strided ROIs) and ROIs."""
+    """Owns an ``opm_batch*``: persistent launches of the fused projections
+    (z-MIP, y-MIP, z-sum, arg-max) over many uint16 stacks, channels
+    (strided ROIs) and ROIs."""
 
     def __init__(self, max_items: int, max_units: int = 1 << 20):
         lib = load()
@@ -401,23 +418,14 @@ class Batch:
     def handle(self):
         return self._h
 
-    def set(self, items, kchunk: int = 0):
-        """items: sequence of dicts {plan, raw, zmip?, ymip?, row_pitch?, plane_pitch?};
-        raw is a uint16 CUDA tensor (a view is fine: its data pointer is the
-        ROI origin and the pitches are elements)."""
-        arr = (opm_batch_item * max(1, len(items)))()
-        keep = []
-        for i, it in enumerate(items):
-            raw = it["raw"]
-            if not raw.is_cuda:
-                raise ValueError("raw must be a CUDA tensor")
-            z, y = it.get("zmip"), it.get("ymip")
-            arr[i] = opm_batch_item(it["plan"].handle.value, raw.data_ptr(), int(it.get("row_pitch", 0)),
-                                    int(it.get("plane_pitch", 0)), z.data_ptr() if z is not None else None,
-                                    y.data_ptr() if y is not None else None)
-            keep.append((it["plan"], raw, z, y))
-        _check(load().opm_batch_set(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items), int(kchunk)),
-               "opm_batch_set")
+    def set(self, items, kchunk: int = 0, shape: int = OPM_SHAPE_AUTO):
+        """items: sequence of dicts {plan, raw, zmip?, ymip?, zsum?, argz?,
+        row_pitch?, plane_pitch?}; raw is a uint16 CUDA tensor (a view is
+        fine: its data pointer is the ROI origin and the pitches are
+        elements).  shape: an OPM_SHAPE_* kernel shape."""
+        arr, keep = _batch_items(items)
+        _check(load().opm_batch_set(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items), int(kchunk),
+                                    int(shape)), "opm_batch_set")
         self._keep = keep
 
     def upload(self, stream=None):
@@ -442,9 +450,11 @@ class Batch:
         u = ctypes.c_int64()
         sm = ctypes.c_int()
         gc = ctypes.c_int()
-        _check(load().opm_batch_info(self._h, ctypes.byref(n), ctypes.byref(u), ctypes.byref(sm), ctypes.byref(gc)),
-               "opm_batch_info")
-        return {"items": n.value, "units": u.value, "smem_bytes": sm.value, "graph_captures": gc.value}
+        sh = ctypes.c_int()
+        _check(load().opm_batch_info(self._h, ctypes.byref(n), ctypes.byref(u), ctypes.byref(sm), ctypes.byref(gc),
+                                     ctypes.byref(sh)), "opm_batch_info")
+        return {"items": n.value, "units": u.value, "smem_bytes": sm.value, "graph_captures": gc.value,
+                "shape": sh.value}
 
     def check(self):
         _check(load().opm_batch_check(self._h), "opm_batch_check")

@@ -30,6 +30,7 @@
 #include <string>
 
 #include "opm_sched.h"
+#include "opm_gen.cuh"
 #include "opm_periodic.cuh"
 
 namespace opm {
@@ -37,25 +38,36 @@ namespace opm {
 namespace {
 
 struct BatchHdr {
-  int n_units;
+  int n_units;          // units of the fast (or periodic) kernel
   int n_segs;
   unsigned off_units;
   unsigned off_segs;
   int n_lists;
   unsigned off_lists;
-  int pad[2];
+  int n_gunits;         // units of the general kernel
+  unsigned off_gunits;
+  int n_glists;
+  unsigned off_glists;
+  int pad[6];
 };
+static_assert(sizeof(BatchHdr) == 64, "hdr");
 
 constexpr size_t kOffItems = 256;
 
 struct BatchItemDev {  // 64-byte aligned through its tensor map
   CUtensorMap tmap;      // raw stack of the item, box {128, 1, P}
-  const FastRow* frow;   // plan tables, [ntile][nz]
+  const FastRow* frow;   // fast-kernel tables, [ntile][nz] (fast items)
   const int* fnlo;       // [ntile][nz]
+  const Split* A;        // split tables (general items)
+  const Split* B;
   float* zmip;
   float* ymip;
+  float* zsum;
+  int32_t* argz;
   int nz, ny, nx, P;
+  int linear;
 };
+static_assert(sizeof(BatchItemDev) == 256, "item");
 
 struct __align__(16) BatchSeg {
   float* ptr;
@@ -64,10 +76,11 @@ struct __align__(16) BatchSeg {
 
 constexpr size_t cal256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Bytes of a work-list image with room for max_items items and max_units units.
+// Bytes of a work-list image with room for max_items items and max_units
+// units (of both kernels together).
 constexpr size_t worklist_bytes(size_t max_items, size_t max_units) {
   return kOffItems + cal256(sizeof(BatchItemDev) * max_items) + cal256(sizeof(BatchSeg) * 2 * max_items) +
-         cal256(sizeof(int) * (kMaxLists + 1)) + sizeof(WorkUnit) * max_units;
+         2 * cal256(sizeof(int) * (kMaxLists + 1)) + sizeof(WorkUnit) * max_units;
 }
 
 __global__ void k_batch_zero(const unsigned char* __restrict__ wl) {
@@ -143,13 +156,19 @@ k_batch_fast(const unsigned char* __restrict__ wl, int Pl, unsigned* err) {
 // The same persistent loop with the periodic kernel's producer and compute
 // warps (opm_periodic.cuh), for batches whose items all belong to the plan
 // family pixel/step = Pp/Qq.
-template <int Pp, int Qq>
-__global__ void __launch_bounds__(per::Cfg<kPerRun>::kThreads, kPerCtasPerSm)
+// Resident CTAs per SM the periodic batch kernel is compiled for: 4 with 32
+// columns j per warp (96 threads), 3 with 16 (160 threads, whose register
+// share at 4 would spill).
+template <int RUN>
+constexpr int per_minb() { return RUN == 16 ? 3 : kPerCtasPerSm; }
+
+template <int Pp, int Qq, int RUN>
+__global__ void __launch_bounds__(per::Cfg<RUN>::kThreads, per_minb<RUN>())
 k_batch_per(const unsigned char* __restrict__ wl, int Pl, unsigned* err) {
   extern __shared__ __align__(128) unsigned char smem[];
   const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(wl);
   const PerRing ring = per_ring(smem, kPerStages, Pl);
-  per_ring_init(ring, per::Cfg<kPerRun>::kCW);
+  per_ring_init(ring, per::Cfg<RUN>::kCW);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   int g = 0;
@@ -191,14 +210,76 @@ k_batch_per(const unsigned char* __restrict__ wl, int Pl, unsigned* err) {
       __syncwarp();
       ok = per_produce(jb, ring, g, err, lane);
     } else {
-      ok = per_consume<kPerRun, Pp, Qq>(jb, ring, g, err, warp - 1, lane);
+      ok = per_consume<RUN, Pp, Qq>(jb, ring, g, err, warp - 1, lane);
     }
   }
   if (warp == 0) per_drain(ring, g, ok, err);
 }
 
+// The general kernel's persistent loop (opm_gen.cuh) over the items the
+// fast kernels do not take: one unit per (x-tile, j-tile) and whole row
+// band, on one ring of slab depth Pg whose stage counter carries on across
+// units.
+constexpr int kGenCtasPerSm = 2;
+
+__global__ void __launch_bounds__(kThreads, kGenCtasPerSm)
+k_batch_gen(const unsigned char* __restrict__ wl, int Pg, unsigned* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(wl);
+  const GenRing<uint16_t> ring{smem, Pg};
+  gen_ring_init<uint16_t>(ring);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  int g = 0;
+  bool ok = true;
+  int l = (int)blockIdx.x - (int)gridDim.x;
+  int u = 0, uend = 0;
+#pragma unroll 1
+  while (ok) {
+    if (u >= uend) {
+      const int* lists = reinterpret_cast<const int*>(wl + hdr->off_glists);
+      do {
+        l += gridDim.x;
+        if (l >= hdr->n_glists) break;
+        u = lists[l];
+        uend = lists[l + 1];
+      } while (u >= uend);
+      if (u >= uend) break;
+    }
+    const WorkUnit un = reinterpret_cast<const WorkUnit*>(wl + hdr->off_gunits)[u++];
+    const BatchItemDev* it = reinterpret_cast<const BatchItemDev*>(wl + kOffItems) + un.item;
+    GenJob jb;
+    jb.tmap = &it->tmap;
+    jb.A = it->A;
+    jb.B = it->B;
+    jb.linear = it->linear;
+    jb.ny = it->ny;
+    jb.nz = it->nz;
+    jb.nx = it->nx;
+    jb.P = it->P;
+    jb.j0 = un.jt * kTileJ;
+    jb.xbase = un.xt * kX;
+    jb.ks = un.ks;
+    jb.ke = un.ke;
+    jb.zmip = it->zmip;
+    jb.zsum = it->zsum;
+    jb.ymip = it->ymip;
+    jb.argz = it->argz;
+    if (warp == 0) {
+      if (lane == 0)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(jb.tmap) : "memory");
+      __syncwarp();
+      ok = gen_produce<uint16_t>(jb, ring, g, err, lane);
+    } else {
+      ok = gen_consume<uint16_t>(jb, ring, g, err, warp - 1, lane);
+    }
+  }
+  if (warp == 0) gen_drain<uint16_t>(ring, g, ok, err, lane);
+}
+
 // Shared memory of a batch launch for slab depth Pl (family 0: k_batch_fast).
 size_t batch_smem(int Pl, int family) { return family ? per::total(kPerStages, Pl) : fast::total(Pl); }
+size_t batch_gen_smem(int Pg) { return gen::total<uint16_t>(Pg); }
 
 PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -219,16 +300,32 @@ PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
 struct WorkList {
   size_t used;  // bytes of the image to copy
   int n_items, n_units, n_segs, n_lists, Pl;
-  int family;  // kFamilies index + 1 shared by every item, or 0
+  int family;   // kFamilies index + 1 of the periodic kernel, or 0 (fast kernel)
+  int n_gunits; // units of the general kernel
+  int Pg;       // its slab depth (deepest general item)
+  int run;      // columns j per compute warp of the periodic kernel (32 or 16)
+  int shape;    // opm_shape the list was built for (never AUTO)
 };
+
+constexpr WorkList kEmptyWorkList = {kOffItems, 0, 0, 0, 0, 2, 0, 0, 2, kPerRun, OPM_SHAPE_PER_J32X2};
 
 // Builds the work-list image of `items` into `stage` (room for max_items
 // items and max_units units; 64-byte aligned).  Allocates nothing on
 // success.  `limit_what` names the capacity in error messages.
-opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, int device, int nlists,
+//
+// An item goes to the fast kernels when its plan is fast-eligible and it
+// asks for z-MIP / y-MIP only (units: kchunk-row chunks of every tile's
+// band), else to the general kernel (units: whole bands; a tile with an
+// empty band still gets a unit when the item has a z output, which the
+// unit's epilogue writes).  Zeroed outputs: every y-MIP and the z-MIP of
+// fast items (both combined by atomic max); the general kernel writes its
+// z outputs outright.
+opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, int shape, int device, int nlists,
                           unsigned char* stage, int max_items, int64_t max_units, const char* limit_what,
                           WorkList* out) {
   if (n_items < 0) return fail(OPM_ERR_INVALID_ARG, "n_items must be >= 0");
+  if (shape < OPM_SHAPE_AUTO || shape > OPM_SHAPE_GEN_J8X4) return fail(OPM_ERR_INVALID_ARG, "unknown shape");
+  const bool gen_all = shape == OPM_SHAPE_GEN_J8X4;
   if (n_items > max_items)
     return fail(OPM_ERR_UNSUPPORTED, std::to_string(n_items) + " items exceed the " + limit_what + "'s limit of " +
                                          std::to_string(max_items));
@@ -238,85 +335,131 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
   if (!batch_encode_fn()) return fail(OPM_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is unavailable");
   const size_t off_segs = cal256(kOffItems + sizeof(BatchItemDev) * (size_t)n_items);
   const size_t off_lists = cal256(off_segs + sizeof(BatchSeg) * 2 * (size_t)n_items);
-  const size_t off_units = cal256(off_lists + sizeof(int) * (size_t)(nlists + 1));
+  const size_t off_glists = cal256(off_lists + sizeof(int) * (size_t)(nlists + 1));
+  const size_t off_units = cal256(off_glists + sizeof(int) * (size_t)(nlists + 1));
   BatchItemDev* hitems = reinterpret_cast<BatchItemDev*>(stage + kOffItems);
   BatchSeg* hsegs = reinterpret_cast<BatchSeg*>(stage + off_segs);
   int* hlists = reinterpret_cast<int*>(stage + off_lists);
+  int* hglists = reinterpret_cast<int*>(stage + off_glists);
   WorkUnit* hunits = reinterpret_cast<WorkUnit*>(stage + off_units);
   int64_t nunits = 0;
-  int Pl = 2, nseg = 0, family = -1;
-  for (int i = 0; i < n_items; ++i) {
-    const opm_batch_item& it = items[i];
-    const opm_plan* p = it.plan;
-    if (!p || !it.raw) return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": NULL plan or raw");
-    if (p->device != device)
-      return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) + ": plan on another device");
-    if (!plan_fast_ok(p))
-      return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
-                                           ": plan not eligible (needs pixel <= step and ny >= 32)");
-    const int64_t rp = it.row_pitch ? it.row_pitch : p->ncols;
-    const int64_t pp = it.plane_pitch ? it.plane_pitch : p->nrows * rp;
-    if (rp < p->ncols || pp < p->nrows * rp)
-      return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": pitches smaller than the ROI");
-    if ((uintptr_t)it.raw % 16 != 0 || rp % 8 != 0 || pp % 8 != 0)
-      return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
-                                           ": raw must be 16-byte aligned and pitches multiples of 8 elements");
-    BatchItemDev& d = hitems[i];
-    std::memset(&d, 0, sizeof(d));
-    const cuuint64_t dims[3] = {(cuuint64_t)p->ncols, (cuuint64_t)p->nrows, (cuuint64_t)p->nscan};
-    const cuuint64_t strides[2] = {(cuuint64_t)rp * 2, (cuuint64_t)pp * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kX, 1u, (cuuint32_t)p->P};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult cr = batch_encode_fn()(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t*>(it.raw), dims,
-                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS)
-      return fail(OPM_ERR_CUDA, "item " + std::to_string(i) + ": cuTensorMapEncodeTiled failed (" +
-                                    std::to_string((int)cr) + ")");
-    d.frow = p->view.frow;
-    d.fnlo = p->view.fnlo;
-    d.zmip = it.zmip;
-    d.ymip = it.ymip;
-    d.nz = (int)p->nz;
-    d.ny = (int)p->ny;
-    d.nx = (int)p->nx;
-    d.P = p->P;
-    Pl = std::max(Pl, p->P);
-    family = (family < 0 || family == p->family) ? p->family : 0;
-    if (it.zmip) hsegs[nseg++] = BatchSeg{it.zmip, (long long)(p->ny * p->nx)};
-    if (it.ymip) hsegs[nseg++] = BatchSeg{it.ymip, (long long)(p->nz * p->nx)};
-    if (!it.zmip && !it.ymip) continue;
-    const int xtiles = (int)((p->nx + kX - 1) / kX);
-    const int jtiles = (int)((p->ny + kTileJ - 1) / kTileJ);
-    for (int jt = 0; jt < jtiles; ++jt) {
-      const Band bd = p->hBand[jt];
-      for (int c0 = (bd.lo / kchunk) * kchunk; c0 < bd.hi; c0 += kchunk) {
-        const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + kchunk);
-        if (ks >= ke) continue;
-        if (nunits + xtiles > max_units)
-          return fail(OPM_ERR_UNSUPPORTED, std::string("the items need more than the ") + limit_what + "'s limit of " +
-                                               std::to_string(max_units) + " work units (raise kchunk or split)");
-        for (int xt = 0; xt < xtiles; ++xt) hunits[nunits++] = WorkUnit{i, xt, jt, ks, ke, 0, 0, 0};
+  int Pl = 2, Pg = 2, nseg = 0, family = -1, nfast = 0;
+  // first pass: fast items' units; second pass: general items' units after them
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < n_items; ++i) {
+      const opm_batch_item& it = items[i];
+      const opm_plan* p = it.plan;
+      if (pass == 0) {
+        if (!p || !it.raw) return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": NULL plan or raw");
+        if (p->device != device)
+          return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) + ": plan on another device");
+        if (p->P > 256)
+          return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) + ": slab depth beyond 256 planes");
+        const int64_t rp = it.row_pitch ? it.row_pitch : p->ncols;
+        const int64_t pp = it.plane_pitch ? it.plane_pitch : p->nrows * rp;
+        if (rp < p->ncols || pp < p->nrows * rp)
+          return fail(OPM_ERR_INVALID_ARG, "item " + std::to_string(i) + ": pitches smaller than the ROI");
+        if ((uintptr_t)it.raw % 16 != 0 || rp % 8 != 0 || pp % 8 != 0)
+          return fail(OPM_ERR_UNSUPPORTED, "item " + std::to_string(i) +
+                                               ": raw must be 16-byte aligned and pitches multiples of 8 elements");
+        BatchItemDev& d = hitems[i];
+        std::memset(&d, 0, sizeof(d));
+        const cuuint64_t dims[3] = {(cuuint64_t)p->ncols, (cuuint64_t)p->nrows, (cuuint64_t)p->nscan};
+        const cuuint64_t strides[2] = {(cuuint64_t)rp * 2, (cuuint64_t)pp * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)kX, 1u, (cuuint32_t)p->P};
+        const cuuint32_t estr[3] = {1u, 1u, 1u};
+        CUresult cr = batch_encode_fn()(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t*>(it.raw),
+                                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS)
+          return fail(OPM_ERR_CUDA, "item " + std::to_string(i) + ": cuTensorMapEncodeTiled failed (" +
+                                        std::to_string((int)cr) + ")");
+        d.frow = p->view.frow;
+        d.fnlo = p->view.fnlo;
+        d.A = p->view.A;
+        d.B = p->view.B;
+        d.linear = p->view.linear;
+        d.zmip = it.zmip;
+        d.ymip = it.ymip;
+        d.zsum = it.zsum;
+        d.argz = it.argz;
+        d.nz = (int)p->nz;
+        d.ny = (int)p->ny;
+        d.nx = (int)p->nx;
+        d.P = p->P;
+      }
+      const bool fast = !gen_all && plan_fast_ok(p) && !it.zsum && !it.argz;
+      if (fast != (pass == 0)) continue;
+      const bool zout = it.zmip || it.zsum || it.argz;
+      if (!zout && !it.ymip) continue;
+      if (fast) {
+        Pl = std::max(Pl, p->P);
+        family = (family < 0 || family == p->family) ? p->family : 0;
+        if (it.zmip) hsegs[nseg++] = BatchSeg{it.zmip, (long long)(p->ny * p->nx)};
+      } else {
+        Pg = std::max(Pg, p->P);
+      }
+      if (it.ymip) hsegs[nseg++] = BatchSeg{it.ymip, (long long)(p->nz * p->nx)};
+      const int xtiles = (int)((p->nx + kX - 1) / kX);
+      const int jtiles = (int)((p->ny + kTileJ - 1) / kTileJ);
+      for (int jt = 0; jt < jtiles; ++jt) {
+        const Band bd = p->hBand[jt];
+        const int step = fast ? kchunk : std::max(1, bd.hi - bd.lo);
+        const int cstart = fast ? (bd.lo / kchunk) * kchunk : bd.lo;
+        const bool empty_unit = !fast && zout && bd.lo >= bd.hi;
+        for (int c0 = cstart; c0 < bd.hi || (empty_unit && c0 == cstart); c0 += step) {
+          const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + step);
+          if (ks >= ke && !empty_unit) continue;
+          if (nunits + xtiles > max_units)
+            return fail(OPM_ERR_UNSUPPORTED, std::string("the items need more than the ") + limit_what +
+                                                 "'s limit of " + std::to_string(max_units) +
+                                                 " work units (raise kchunk or split)");
+          for (int xt = 0; xt < xtiles; ++xt)
+            hunits[nunits++] = WorkUnit{i, xt, jt, ks, std::max(ks, ke), 0, 0, 0};
+        }
       }
     }
+    if (pass == 0) nfast = (int)nunits;
   }
-  // balanced lists of units, one per persistent CTA
-  schedule_lpt(hunits, (int)nunits, nlists, hlists);
+  const int ngen = (int)nunits - nfast;
+  // balanced lists of units, one per persistent CTA, for each kernel
+  schedule_lpt(hunits, nfast, nlists, hlists);
+  schedule_lpt(hunits + nfast, ngen, nlists, hglists);
   BatchHdr* hdr = reinterpret_cast<BatchHdr*>(stage);
   std::memset(hdr, 0, sizeof(*hdr));
-  hdr->n_units = (int)nunits;
+  hdr->n_units = nfast;
   hdr->n_segs = nseg;
   hdr->off_units = (unsigned)off_units;
   hdr->off_segs = (unsigned)off_segs;
   hdr->n_lists = nlists;
   hdr->off_lists = (unsigned)off_lists;
+  hdr->n_gunits = ngen;
+  hdr->off_gunits = (unsigned)(off_units + sizeof(WorkUnit) * (size_t)nfast);
+  hdr->n_glists = nlists;
+  hdr->off_glists = (unsigned)off_glists;
   out->used = off_units + sizeof(WorkUnit) * (size_t)nunits;
   out->n_items = n_items;
-  out->n_units = (int)nunits;
+  out->n_units = nfast;
   out->n_segs = nseg;
   out->n_lists = nlists;
   out->Pl = Pl;
-  out->family = family < 0 ? 0 : family;
+  // the fast items' kernel: the periodic one (32 or 16 columns j per warp)
+  // needs one family shared by all of them, else the fast kernel runs them
+  if (family < 0) family = 0;
+  if (gen_all) {
+    family = 0;
+  } else if (shape == OPM_SHAPE_AUTO) {
+    shape = family ? OPM_SHAPE_PER_J32X2 : OPM_SHAPE_FAST_J8X4;
+  } else if (shape == OPM_SHAPE_FAST_J8X4 || family == 0) {
+    shape = OPM_SHAPE_FAST_J8X4;
+    family = 0;
+  }
+  out->family = family;
+  out->n_gunits = ngen;
+  out->Pg = Pg;
+  out->run = shape == OPM_SHAPE_PER_J16X2 ? 16 : kPerRun;
+  out->shape = shape;
   return OPM_OK;
 }
 
@@ -325,25 +468,58 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
 constexpr int kZeroRows = 32;
 
 template <int F>
-void launch_batch_per(const unsigned char* dev_wl, int Pl, int family, int grid, unsigned* err, cudaStream_t s) {
+void launch_batch_per(const unsigned char* dev_wl, const WorkList& wl, int grid, unsigned* err, cudaStream_t s) {
   if constexpr (F < kNumFamilies) {
-    if (family - 1 != F) return launch_batch_per<F + 1>(dev_wl, Pl, family, grid, err, s);
-    k_batch_per<kFamilies[F].p, kFamilies[F].q>
-        <<<grid, per::Cfg<kPerRun>::kThreads, batch_smem(Pl, family), s>>>(dev_wl, Pl, err);
+    if (wl.family - 1 != F) return launch_batch_per<F + 1>(dev_wl, wl, grid, err, s);
+    constexpr int Pp = kFamilies[F].p, Qq = kFamilies[F].q;
+    const size_t smem = batch_smem(wl.Pl, wl.family);
+    if (wl.run == 16)
+      k_batch_per<Pp, Qq, 16><<<grid, per::Cfg<16>::kThreads, smem, s>>>(dev_wl, wl.Pl, err);
+    else
+      k_batch_per<Pp, Qq, kPerRun><<<grid, per::Cfg<kPerRun>::kThreads, smem, s>>>(dev_wl, wl.Pl, err);
   }
 }
 
-// Zero kernel, then `grid` persistent CTAs (none when grid == 0), on `s`.
-cudaError_t launch_worklist(const unsigned char* dev_wl, int Pl, int family, int grid, unsigned* err,
+// Zero kernel, then the fast (or periodic) kernel's `grid` persistent CTAs
+// when the list has fast units, then the general kernel's `ggrid` CTAs when
+// it has general units, all on `s`.
+cudaError_t launch_worklist(const unsigned char* dev_wl, const WorkList& wl, int grid, int ggrid, unsigned* err,
                             cudaStream_t s) {
   k_batch_zero<<<dim3(64, kZeroRows), 256, 0, s>>>(dev_wl);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || grid == 0) return e;
-  if (family)
-    launch_batch_per<0>(dev_wl, Pl, family, grid, err, s);
-  else
-    k_batch_fast<<<grid, kThreads, fast::total(Pl), s>>>(dev_wl, Pl, err);
-  return cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (grid > 0) {
+    if (wl.family)
+      launch_batch_per<0>(dev_wl, wl, grid, err, s);
+    else
+      k_batch_fast<<<grid, kThreads, fast::total(wl.Pl), s>>>(dev_wl, wl.Pl, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (ggrid > 0) {
+    k_batch_gen<<<ggrid, kThreads, batch_gen_smem(wl.Pg), s>>>(dev_wl, wl.Pg, err);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// Persistent grids of the two kernels for `ctas_per_sm` (the general kernel
+// takes at most kGenCtasPerSm per SM); `all` gives full grids whatever the
+// unit counts, as a captured graph needs.
+void batch_grids(const WorkList& wl, int nsm, int ctas_per_sm, bool all, int* grid, int* ggrid) {
+  const int64_t fmax = (int64_t)nsm * ctas_per_sm;
+  const int64_t gmax = (int64_t)nsm * std::min(ctas_per_sm, kGenCtasPerSm);
+  *grid = wl.n_units == 0 ? 0 : (int)(all ? fmax : std::min<int64_t>(wl.n_units, fmax));
+  *ggrid = wl.n_gunits == 0 ? 0 : (int)(all ? gmax : std::min<int64_t>(wl.n_gunits, gmax));
+}
+
+// Shared memory check of a prepared list against the device's opt-in limit.
+opm_status batch_check_smem(const WorkList& wl, int smem_optin) {
+  if (wl.n_units > 0 && (int)batch_smem(wl.Pl, wl.family) > smem_optin)
+    return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
+  if (wl.n_gunits > 0 && (int)batch_gen_smem(wl.Pg) > smem_optin)
+    return fail(OPM_ERR_UNSUPPORTED, "general items' slab depth needs too much shared memory");
+  return OPM_OK;
 }
 
 template <typename K>
@@ -357,7 +533,8 @@ cudaError_t set_kernel_smem(K kern, int smem_optin) {
 template <int F>
 cudaError_t set_per_attrs(int smem_optin) {
   if constexpr (F < kNumFamilies) {
-    cudaError_t e = set_kernel_smem(k_batch_per<kFamilies[F].p, kFamilies[F].q>, smem_optin);
+    cudaError_t e = set_kernel_smem(k_batch_per<kFamilies[F].p, kFamilies[F].q, kPerRun>, smem_optin);
+    if (e == cudaSuccess) e = set_kernel_smem(k_batch_per<kFamilies[F].p, kFamilies[F].q, 16>, smem_optin);
     return e == cudaSuccess ? set_per_attrs<F + 1>(smem_optin) : e;
   }
   return cudaSuccess;
@@ -365,6 +542,7 @@ cudaError_t set_per_attrs(int smem_optin) {
 
 cudaError_t set_fast_attrs(int smem_optin) {
   cudaError_t e = set_kernel_smem(k_batch_fast, smem_optin);
+  if (e == cudaSuccess) e = set_kernel_smem(k_batch_gen, smem_optin);
   return e == cudaSuccess ? set_per_attrs<0>(smem_optin) : e;
 }
 
@@ -373,6 +551,8 @@ cudaError_t set_fast_attrs(int smem_optin) {
 }  // namespace opm
 
 using namespace opm;
+
+constexpr int kGraphCache = 4;  // captured launch shapes kept per batch
 
 struct opm_batch {
   int max_items;
@@ -387,9 +567,16 @@ struct opm_batch {
   bool pending;          // an upload was recorded since the last wait
   WorkList wl;           // the prepared content
   int attr_set;
-  cudaStream_t capture;  // private stream the graph is captured on
-  cudaGraphExec_t graph; // zero + persistent kernels for (graph_Pl, graph_family, graph_grid)
-  int graph_Pl, graph_family, graph_grid, graph_captures;
+  cudaStream_t capture;  // private stream the graphs are captured on
+  // Captured launches (zero kernel + persistent kernels), one per launch
+  // shape: kernel shape, periodic family and run, slab depths and grids.
+  struct Graph {
+    cudaGraphExec_t exec;
+    int key[7];
+    unsigned long long used;  // launch counter at the last use
+  } graphs[kGraphCache];
+  unsigned long long launches;
+  int graph_captures;
 };
 
 extern "C" {
@@ -424,7 +611,7 @@ opm_status opm_batch_create(int max_items, int64_t max_units, opm_batch** out) {
     return st;
   }
   std::memset(b->host, 0, kOffItems);
-  b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2, 0};
+  b->wl = kEmptyWorkList;
   *out = b;
   return OPM_OK;
 }
@@ -433,7 +620,8 @@ opm_status opm_batch_destroy(opm_batch* b) {
   if (!b) return OPM_OK;
   cudaError_t e = cudaSuccess, e2;
   if (b->uploaded && (e2 = cudaEventSynchronize(b->uploaded)) != cudaSuccess) e = e2;
-  if (b->graph && (e2 = cudaGraphExecDestroy(b->graph)) != cudaSuccess) e = e2;
+  for (auto& gr : b->graphs)
+    if (gr.exec && (e2 = cudaGraphExecDestroy(gr.exec)) != cudaSuccess) e = e2;
   if (b->capture && (e2 = cudaStreamDestroy(b->capture)) != cudaSuccess) e = e2;
   if (b->dev && (e2 = cudaFree(b->dev)) != cudaSuccess) e = e2;
   if (b->host && (e2 = cudaFreeHost(b->host)) != cudaSuccess) e = e2;
@@ -442,7 +630,7 @@ opm_status opm_batch_destroy(opm_batch* b) {
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "opm_batch_destroy");
 }
 
-opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk) {
+opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items, int kchunk, int shape) {
   if (!b || (!items && n_items > 0)) return fail(OPM_ERR_INVALID_ARG, "batch or items is NULL");
   if (n_items < 0 || n_items > b->max_items)
     return fail(OPM_ERR_INVALID_ARG, "n_items must lie in [0, max_items]");
@@ -454,12 +642,12 @@ opm_status opm_batch_set(opm_batch* b, const opm_batch_item* items, int n_items,
   }
   WorkList wl;
   const int nlists = std::min(b->nsm * 4, kMaxLists);
-  opm_status st = build_worklist(items, n_items, kchunk, b->device, nlists, b->host, b->max_items, b->max_units,
-                                 "batch", &wl);
+  opm_status st = build_worklist(items, n_items, kchunk, shape, b->device, nlists, b->host, b->max_items,
+                                 b->max_units, "batch", &wl);
   if (st != OPM_OK) {
     // leave an empty, valid image behind
     std::memset(b->host, 0, kOffItems);
-    b->wl = WorkList{kOffItems, 0, 0, 0, 0, 2, 0};
+    b->wl = kEmptyWorkList;
     return st;
   }
   b->wl = wl;
@@ -479,8 +667,8 @@ opm_status opm_batch_upload(opm_batch* b, void* stream) {
 static opm_status batch_prepare_launch(opm_batch* b, int& ctas_per_sm) {
   if (ctas_per_sm < 0 || ctas_per_sm > 4) return fail(OPM_ERR_INVALID_ARG, "ctas_per_sm must lie in [0, 4]");
   if (ctas_per_sm == 0) ctas_per_sm = 4;
-  if ((int)batch_smem(b->wl.Pl, b->wl.family) > b->smem_optin)
-    return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
+  opm_status st = batch_check_smem(b->wl, b->smem_optin);
+  if (st != OPM_OK) return st;
   if (!b->attr_set) {
     cudaError_t e = set_fast_attrs(b->smem_optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_batch_fast)");
@@ -493,8 +681,9 @@ opm_status opm_batch_launch(opm_batch* b, int ctas_per_sm, void* stream) {
   if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
   opm_status st = batch_prepare_launch(b, ctas_per_sm);
   if (st != OPM_OK) return st;
-  const int grid = (int)std::min<int64_t>(b->wl.n_units, (int64_t)b->nsm * ctas_per_sm);
-  cudaError_t e = launch_worklist(b->dev, b->wl.Pl, b->wl.family, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
+  int grid = 0, ggrid = 0;
+  batch_grids(b->wl, b->nsm, ctas_per_sm, false, &grid, &ggrid);
+  cudaError_t e = launch_worklist(b->dev, b->wl, grid, ggrid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
                                   static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "opm_batch_launch");
 }
@@ -503,40 +692,54 @@ opm_status opm_batch_launch_graph(opm_batch* b, int ctas_per_sm, void* stream) {
   if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
   opm_status st = batch_prepare_launch(b, ctas_per_sm);
   if (st != OPM_OK) return st;
-  const int grid = b->nsm * ctas_per_sm;  // every CTA reads the unit count from the device header
-  if (!b->graph || b->graph_Pl != b->wl.Pl || b->graph_family != b->wl.family || b->graph_grid != grid) {
-    if (b->graph) {
-      cudaError_t e = cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
+  // full grids: every CTA reads the unit counts from the device header
+  int grid = 0, ggrid = 0;
+  batch_grids(b->wl, b->nsm, ctas_per_sm, true, &grid, &ggrid);
+  const int key[7] = {grid ? b->wl.shape : 0, grid ? b->wl.family : 0, grid ? b->wl.run : 0,
+                      grid ? b->wl.Pl : 0,    grid,                     ggrid ? b->wl.Pg : 0, ggrid};
+  opm_batch::Graph* hit = nullptr;
+  for (auto& gr : b->graphs)
+    if (gr.exec && std::equal(key, key + 7, gr.key)) hit = &gr;
+  b->launches += 1;
+  if (!hit) {
+    // an empty slot, else the least recently used one
+    for (auto& gr : b->graphs)
+      if (!hit || (hit->exec && (!gr.exec || gr.used < hit->used))) hit = &gr;
+    if (hit->exec) {
+      cudaError_t e = cudaGraphExecDestroy(hit->exec);
+      hit->exec = nullptr;
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphExecDestroy");
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaError_t le = launch_worklist(b->dev, b->wl.Pl, b->wl.family, grid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
+    cudaError_t le = launch_worklist(b->dev, b->wl, grid, ggrid, reinterpret_cast<unsigned*>(b->dev + b->bytes),
                                      b->capture);
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess) e = le;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&hit->exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      b->graph = nullptr;
+      hit->exec = nullptr;
       return cuda_fail(e, "capturing the batch launch");
     }
-    b->graph_Pl = b->wl.Pl;
-    b->graph_family = b->wl.family;
-    b->graph_grid = grid;
+    std::copy(key, key + 7, hit->key);
     b->graph_captures += 1;
   }
-  cudaError_t e = cudaGraphLaunch(b->graph, static_cast<cudaStream_t>(stream));
+  hit->used = b->launches;
+  cudaError_t e = cudaGraphLaunch(hit->exec, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "cudaGraphLaunch");
 }
 
-opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes, int* graph_captures) {
+opm_status opm_batch_info(const opm_batch* b, int* n_items, int64_t* n_units, int* smem_bytes, int* graph_captures,
+                          int* shape) {
   if (!b) return fail(OPM_ERR_INVALID_ARG, "batch is NULL");
+  if (shape) *shape = b->wl.shape;
   if (n_items) *n_items = b->wl.n_items;
-  if (n_units) *n_units = b->wl.n_units;
-  if (smem_bytes) *smem_bytes = (int)batch_smem(b->wl.Pl, b->wl.family);
+  if (n_units) *n_units = (int64_t)b->wl.n_units + b->wl.n_gunits;
+  if (smem_bytes)
+    *smem_bytes = (int)std::max(b->wl.n_units ? batch_smem(b->wl.Pl, b->wl.family) : 0,
+                                b->wl.n_gunits ? batch_gen_smem(b->wl.Pg) : 0);
   if (graph_captures) *graph_captures = b->graph_captures;
   return OPM_OK;
 }
@@ -639,17 +842,18 @@ extern "C" opm_status opm_batch_project_static(const opm_batch_item* items, int 
     // the host image.  The pageable copy returns once its source has been
     // staged, so the image may be rebuilt as soon as it returns.
     std::lock_guard<std::mutex> lk(g_static_mu);
-    st = build_worklist(items, n_items, kchunk, dev, std::min(sd->nsm * 4, kMaxLists), g_static_stage, kStaticItems,
-                        kStaticUnits, "static work list", &wl);
+    st = build_worklist(items, n_items, kchunk, OPM_SHAPE_AUTO, dev, std::min(sd->nsm * 4, kMaxLists),
+                        g_static_stage, kStaticItems, kStaticUnits, "static work list", &wl);
     if (st != OPM_OK) return st;
-    if ((int)batch_smem(wl.Pl, wl.family) > sd->smem_optin)
-      return fail(OPM_ERR_UNSUPPORTED, "batch slab depth needs too much shared memory");
+    st = batch_check_smem(wl, sd->smem_optin);
+    if (st != OPM_OK) return st;
     e = cudaMemcpyAsync(dv, g_static_stage, wl.used, cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);  // error word starts at 0
   if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static upload");
-  const int grid = (int)std::min<int64_t>(wl.n_units, (int64_t)sd->nsm * ctas_per_sm);
-  e = launch_worklist(dv, wl.Pl, wl.family, grid, err, s);
+  int grid = 0, ggrid = 0;
+  batch_grids(wl, sd->nsm, ctas_per_sm, false, &grid, &ggrid);
+  e = launch_worklist(dv, wl, grid, ggrid, err, s);
   if (e != cudaSuccess) return cuda_fail(e, "opm_batch_project_static launch");
   if (check) {
     unsigned word = 0;

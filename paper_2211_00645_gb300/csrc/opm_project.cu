@@ -42,6 +42,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "opm_gen.cuh"
 #include "opm_periodic.cuh"
 
 namespace opm {
@@ -157,249 +158,43 @@ k_project_per(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
 }
 
 // =====================================================================
-// General kernel: every output, uint16 or FP32, any tile, one row per stage.
-namespace gen {
-
-constexpr int S = kStagesGen;
-
-struct __align__(16) RowHdr {
-  int k;           // camera row staged
-  int nlo;         // first staged plane
-  unsigned adv;    // bit j: column j is one plane above column j-1
-  unsigned jump;   // bit j: column j is more than one plane above column j-1
-  unsigned valid;  // bit j: column j lies inside the output grid
-  int ofirst[kNW]; // slab offset of the first column of each compute warp
-  int pad[3];
-};
-static_assert(sizeof(RowHdr) == 48, "hdr");
-
-// slab rows 0..P-1 come from TMA, rows P and P+1 stay zero (columns j >= ny)
-template <typename T>
-__host__ __device__ inline size_t slab_bytes(int P) { return (size_t)(P + 2) * kX * sizeof(T); }
-template <typename T>
-__host__ __device__ inline size_t off_w(int P) { return S * slab_bytes<T>(P); }
-template <typename T>
-__host__ __device__ inline size_t off_o(int P) { return off_w<T>(P) + S * kTileJ * 4; }
-template <typename T>
-__host__ __device__ inline size_t off_hdr(int P) { return off_o<T>(P) + S * kTileJ * 4; }
-template <typename T>
-__host__ __device__ inline size_t off_ybuf(int P) { return off_hdr<T>(P) + S * sizeof(RowHdr); }
-template <typename T>
-__host__ __device__ inline size_t off_bar(int P) { return off_ybuf<T>(P) + S * kX * 4; }
-template <typename T>
-__host__ __device__ inline size_t total(int P) { return off_bar<T>(P) + 2 * S * 8; }
-
-}  // namespace gen
-
+// General kernel (opm_gen.cuh): every output, uint16 or FP32, any tile, one
+// row per stage, one job (a tile's whole row band) per CTA on a grid of
+// (x-tile, j-tile).
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
 k_project_gen(const __grid_constant__ CUtensorMap tmap, const ProjArgs args) {
-  using namespace gen;
   const PlanView& v = args.v;
-  const int P = args.P;
-  const int jt = blockIdx.y + args.jt0;  // grid (x-tile, j-tile): see k_project_fast
-  const int j0 = jt * kTileJ;
-  const int xbase = blockIdx.x * kX;
-  const Band band = v.band[jt];
-  const int ks = band.lo, ke = band.hi;
-  const int nst = ke - ks;
-
   extern __shared__ __align__(128) unsigned char smem[];
-  const int pitch = kX * (int)sizeof(T);
-  float* wtab = reinterpret_cast<float*>(smem + off_w<T>(P));
-  int* otab = reinterpret_cast<int*>(smem + off_o<T>(P));
-  RowHdr* hdr = reinterpret_cast<RowHdr*>(smem + off_hdr<T>(P));
-  float* ybuf = reinterpret_cast<float*>(smem + off_ybuf<T>(P));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + off_bar<T>(P));
-  uint64_t* ydone = full + S;
-  auto slab = [&](int s) { return smem + (size_t)s * slab_bytes<T>(P); };
-
+  const GenRing<T> ring{smem, args.P};
+  gen_ring_init<T>(ring);
+  const int jt = blockIdx.y + args.jt0;
+  const Band band = v.band[jt];
+  GenJob jb;
+  jb.tmap = &tmap;
+  jb.A = v.A;
+  jb.B = v.B;
+  jb.linear = v.linear;
+  jb.ny = v.ny;
+  jb.nz = v.nz;
+  jb.nx = v.nx;
+  jb.P = args.P;
+  jb.j0 = jt * kTileJ;
+  jb.xbase = blockIdx.x * kX;
+  jb.ks = band.lo;
+  jb.ke = band.hi;
+  jb.zmip = args.zmip;
+  jb.zsum = args.zsum;
+  jb.ymip = args.ymip;
+  jb.argz = args.argz;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&ydone[s], kNW);
-    }
-    fence_barrier_init();
-  }
-  for (int s = 0; s < S; ++s) {
-    uint4* z = reinterpret_cast<uint4*>(slab(s) + (size_t)P * pitch);
-    for (int i = threadIdx.x; i < 2 * pitch / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
-  }
-  for (int i = threadIdx.x; i < S * kX; i += kThreads) ybuf[i] = -INFINITY;
-  __syncthreads();
-
+  int g = 0;
   if (warp == 0) {
-    // ------------------------------------------------------ producer warp
-    const int jl = j0 + lane;
-    const bool jvalid = jl < v.ny;
-    const Split a = v.A[jvalid ? jl : v.ny - 1];
-    int kbase = ks;
-    Split bcur = v.B[min(kbase + lane, v.nz - 1)];
-    Split bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
-    bool ok = true;
-    int issued = 0;
-#pragma unroll 1
-    for (int it = 0; it < nst + S && ok; ++it) {
-      if (it >= S) {
-        const int r_it = it - S;
-        const int s = r_it % S;
-        ok = mbar_wait(&ydone[s], (r_it / S) & 1, v.err);
-        if (!ok) break;
-        const int k = hdr[s].k;
-        float* yb = ybuf + s * kX;
-#pragma unroll
-        for (int i = 0; i < kVec; ++i) {
-          const int xl = 32 * i + lane;
-          const int yi = yidx(xl);
-          const float val = yb[yi];
-          yb[yi] = -INFINITY;
-          if (args.ymip && xbase + xl < v.nx) atomic_max_f(args.ymip + (size_t)k * v.nx + xbase + xl, val);
-        }
-        __syncwarp();
-      }
-      if (it < nst) {
-        const int s = it % S;
-        const int k = ks + it;
-        if (k - kbase >= 32) {
-          kbase += 32;
-          bcur = bnext;
-          bnext = v.B[min(kbase + 32 + lane, v.nz - 1)];
-        }
-        Split b;
-        b.i = __shfl_sync(0xffffffffu, bcur.i, k - kbase);
-        b.f = __shfl_sync(0xffffffffu, bcur.f, k - kbase);
-        int n0;
-        float w;
-        plane_weight(a, b, v.linear, n0, w);
-        const int nlo = __shfl_sync(0xffffffffu, n0, 0);
-        int o = n0 - nlo;
-        if (!jvalid) {
-          o = P;  // the two zero rows
-          w = 0.0f;
-        } else if (o < 0 || o > P - 2) {
-          atomicOr(v.err, kErrSlabRange);
-          o = min(max(o, 0), P - 2);
-        }
-        const int op = __shfl_up_sync(0xffffffffu, o, 1);
-        const bool first = (lane % kJT) == 0;
-        const unsigned adv = __ballot_sync(0xffffffffu, !first && o == op + 1);
-        const unsigned jump = __ballot_sync(0xffffffffu, !first && o != op && o != op + 1);
-        const unsigned vmask = __ballot_sync(0xffffffffu, jvalid);
-        wtab[s * kTileJ + lane] = w;
-        otab[s * kTileJ + lane] = o;
-        const int of = __shfl_sync(0xffffffffu, o, (lane % kNW) * kJT);
-        RowHdr& h = hdr[s];
-        if (lane < kNW) h.ofirst[lane] = of;
-        if (lane == 0) {
-          h.k = k;
-          h.nlo = nlo;
-          h.adv = adv;
-          h.jump = jump;
-          h.valid = vmask;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive_tx(&full[s], (unsigned)(P * pitch));
-          tma_load_3d(slab(s), &tmap, &full[s], xbase, k, nlo);
-        }
-        issued = it + 1;
-        __syncwarp();
-      }
-    }
-    if (!ok) {
-      for (int q = max(0, issued - S); q < issued; ++q)
-        (void)mbar_wait(&full[q % S], (q / S) & 1, v.err, 50000000ull);
-    }
-    return;
-  }
-
-  // -------------------------------------------------------- compute warps
-  const int g = warp - 1;
-  const int jg = g * kJT;
-  const unsigned lanebit = (lane < kJT) ? (1u << (jg + lane)) : 0u;
-  float zmax[kJT][kVec], zsum[kJT][kVec];
-  int az[kJT][kVec];
-  const float zinit = ks > 0 ? 0.0f : -INFINITY;  // rows before the band are zero
-#pragma unroll
-  for (int j = 0; j < kJT; ++j)
-#pragma unroll
-    for (int c = 0; c < kVec; ++c) {
-      zmax[j][c] = zinit;
-      zsum[j][c] = 0.0f;
-      az[j][c] = 0;
-    }
-
-#pragma unroll 1
-  for (int it = 0; it < nst; ++it) {
-    const int s = it % S;
-    if (!mbar_wait(&full[s], (it / S) & 1, v.err)) break;
-    const RowHdr& h = hdr[s];
-    const int krow = h.k;
-    const unsigned adv = __ballot_sync(0xffffffffu, (h.adv & lanebit) != 0);
-    const unsigned jump = __ballot_sync(0xffffffffu, (h.jump & lanebit) != 0);
-    const unsigned valid = __ballot_sync(0xffffffffu, (h.valid & lanebit) != 0);
-    const unsigned char* ls = slab(s) + lane * (kVec * (int)sizeof(T));
-    Stream st;
-    stream_reset<T>(st, ls, pitch, h.ofirst[g]);
-    float ym[kVec];
-#pragma unroll
-    for (int c = 0; c < kVec; ++c) ym[c] = -INFINITY;
-#pragma unroll
-    for (int j = 0; j < kJT; ++j) {
-      if (j > 0) {
-        if (adv & (1u << j))
-          stream_step<T>(st, ls, pitch);
-        else if (jump & (1u << j))
-          stream_reset<T>(st, ls, pitch, otab[s * kTileJ + jg + j]);
-      }
-      const float w = wtab[s * kTileJ + jg + j];
-      const f2 w2 = pk(w, w);
-      float val[kVec];
-      upk(fma2(w2, st.d[0], st.a[0]), val[0], val[1]);
-      upk(fma2(w2, st.d[1], st.a[1]), val[2], val[3]);
-#pragma unroll
-      for (int c = 0; c < kVec; ++c) {
-        if (val[c] > zmax[j][c]) {
-          zmax[j][c] = val[c];
-          az[j][c] = krow;
-        }
-        zsum[j][c] += val[c];
-      }
-      if (valid & (1u << j)) {
-#pragma unroll
-        for (int c = 0; c < kVec; ++c) ym[c] = fmaxf(ym[c], val[c]);
-      }
-    }
-    float* yb = ybuf + s * kX;
-#pragma unroll
-    for (int c = 0; c < kVec; ++c) atomic_max_f(yb + yidx(lane * kVec + c), ym[c]);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&ydone[s]);
-  }
-
-  // ------------------------------------------------------------ epilogue
-  const int x = xbase + lane * kVec;
-#pragma unroll
-  for (int j = 0; j < kJT; ++j) {
-    const int jj = j0 + jg + j;
-    if (jj >= v.ny) break;
-    const size_t row = (size_t)jj * v.nx;
-#pragma unroll
-    for (int c = 0; c < kVec; ++c) {
-      if (x + c >= v.nx) break;
-      float zm = zmax[j][c];
-      int a = az[j][c];
-      if (ke < v.nz && zm < 0.0f) {  // rows after the band are exactly zero
-        zm = 0.0f;
-        a = ke;
-      }
-      if (args.zmip) args.zmip[row + x + c] = zm;
-      if (args.zsum) args.zsum[row + x + c] = zsum[j][c];
-      if (args.argz) args.argz[row + x + c] = a;
-    }
+    const bool ok = gen_produce<T>(jb, ring, g, v.err, lane);
+    gen_drain<T>(ring, g, ok, v.err, lane);
+  } else {
+    (void)gen_consume<T>(jb, ring, g, v.err, warp - 1, lane);
   }
 }
 

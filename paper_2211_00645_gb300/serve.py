@@ -359,7 +359,7 @@ class LiveViewServer:
 
     def __init__(self, plans: PlanCache, budget_bytes: int, max_items: int = 256, max_units: int = 1 << 22,
                  kchunk: int = 0, ctas_per_sm: int = 0, max_inflight: int = 2, keep_results: bool = True,
-                 result_bytes: int = 1 << 30):
+                 result_bytes: int = 1 << 30, shape: int = 0):
         import torch
 
         from . import Batch
@@ -374,7 +374,7 @@ class LiveViewServer:
         self.comp = torch.cuda.Stream()
         self.batches = [Batch(max_items, max_units) for _ in range(max_inflight)]
         self.max_items = max_items
-        self.kchunk, self.ctas = kchunk, ctas_per_sm
+        self.kchunk, self.ctas, self.shape = kchunk, ctas_per_sm, shape  # shape: an OPM_SHAPE_* value
         self.max_inflight = max_inflight
         self.keep_results = keep_results
         self._lock = threading.Lock()
@@ -556,7 +556,7 @@ class LiveViewServer:
                 items.append({"plan": r.plan, "raw": r.raw[:, :, c * n:], "row_pitch": C * n,
                               "plane_pitch": r.plan.nrows * C * n, "zmip": r.z[c], "ymip": r.y[c]})
         t_set = time.perf_counter()
-        b.set(items, self.kchunk)
+        b.set(items, self.kchunk, self.shape)
         self.host_set_s += time.perf_counter() - t_set
         for r in ready:
             self.comp.wait_event(r.h2d)

@@ -7,7 +7,7 @@ import pytest
 
 import opm_synth
 import oracle as O
-from gpu_util import assert_close, to_dev
+from gpu_util import TOL, assert_close, check_argz, to_dev
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -116,10 +116,10 @@ def test_batch_graph_replay_equals_eager(lib):
 
 def test_batch_rejects_bad_items(lib):
     b = lib.Batch(max_items=2, max_units=8)
-    coarse = lib.Plan(16, 20, 64, 35.0, 0.05, 0.1)            # pixel > step
-    raw = torch.zeros(coarse.raw_shape, dtype=torch.uint16, device="cuda")
+    deep = lib.Plan(400, 20, 64, 35.0, 0.005, 0.1)            # 31 * pixel/step > 256 planes per slab
+    raw = torch.zeros(deep.raw_shape, dtype=torch.uint16, device="cuda")
     with pytest.raises(lib.OpmError) as e:
-        b.set([{"plan": coarse, "raw": raw, "zmip": torch.empty((coarse.ny, coarse.nx), device="cuda")}])
+        b.set([{"plan": deep, "raw": raw, "zmip": torch.empty((deep.ny, deep.nx), device="cuda")}])
     assert e.value.status == lib.OPM_ERR_UNSUPPORTED
     plan = lib.Plan(64, 128, 128, 30.0, 0.4, 0.115)
     raw = torch.zeros(plan.raw_shape, dtype=torch.uint16, device="cuda")
@@ -181,3 +181,101 @@ def test_graph_launch_with_an_empty_batch(lib):
     torch.cuda.synchronize()
     b.check()
     assert b.info()["units"] == 0
+
+
+# Items the fast kernels do not take: pixel > step, ny < 32, and z-sum /
+# arg-max outputs of a fast-eligible plan, beside a fast item.
+GENERAL = [(16, 20, 64, 35.0, 0.05, 0.1),     # pixel > step
+           (40, 70, 264, 35.0, 0.05, 0.1),    # pixel > step, ragged x tile
+           (6, 10, 136, 35.0, 0.3, 0.1),      # ny = 28
+           (4, 16, 264, 45.0, 0.2, 0.115)]    # ny = 19
+KEYS = ("zmip", "ymip", "zsum", "argz")
+
+
+def _general(lib, seed=0):
+    items, refs = [], []
+
+    def add(shape, keys, s):
+        R = _stack(shape, s)
+        plan = lib.Plan(*shape)
+        it = {"plan": plan, "raw": to_dev(R, torch)}
+        for k in keys:
+            rows = plan.nz if k == "ymip" else plan.ny
+            dt = torch.int32 if k == "argz" else torch.float32
+            it[k] = torch.full((rows, plan.nx), -7, dtype=dt, device="cuda")
+        items.append(it)
+        refs.append((shape, R))
+
+    for i, shape in enumerate(GENERAL):
+        add(shape, KEYS if i % 2 == 0 else ("zmip", "ymip"), 40 + i + seed)
+    add((64, 128, 128, 30.0, 0.4, 0.115), ("zsum", "argz", "ymip"), 50 + seed)   # fast plan, general kernel
+    add((33, 50, 264, 45.0, 0.2, 0.115), ("zmip", "ymip"), 51 + seed)            # fast kernels
+    return items, refs
+
+
+def _outs(items):
+    return [{k: it[k].clone() for k in KEYS if it.get(k) is not None} for it in items]
+
+
+def test_general_items_match_single_and_oracle(lib):
+    items, refs = _general(lib)
+    b = lib.Batch(max_items=8)
+    b.set(items)
+    assert b.info()["units"] > 0
+    b.run()
+    torch.cuda.synchronize()
+    b.check()
+    for it, (shape, R) in zip(items, refs):
+        keys = [k for k in KEYS if it.get(k) is not None]
+        single = lib.project(it["plan"], to_dev(R, torch), **{k: k in keys for k in KEYS})
+        for k in keys:
+            assert torch.equal(it[k], single[k]), (shape, k)
+        g = O.geometry(*shape)
+        Rf = R.astype(np.float64)
+        zmip, zsum, ymip, _ = O.project(Rf, g)
+        ref = {"zmip": zmip, "zsum": zsum, "ymip": ymip}
+        for k in keys:
+            if k != "argz":
+                assert_close(it[k].cpu().numpy(), ref[k], what=f"batch {k} {shape}")
+        if "argz" in keys:
+            check_argz(it["argz"].cpu().numpy(), O.deskew(Rf, g), zmip, TOL * max(np.max(np.abs(zmip)), 1e-30))
+
+
+@pytest.mark.parametrize("kchunk,ctas", [(16, 1), (1000, 3)])
+def test_general_items_graph_static_and_tunables(lib, kchunk, ctas):
+    """Graph replay, the allocation-free call and other tunables give the
+    eager launch's results bit for bit; a new graph is captured when the
+    kinds of items change, and the earlier one stays cached."""
+    items, _ = _general(lib, seed=1)
+    b = lib.Batch(max_items=8)
+    b.set(items)
+    b.run()
+    torch.cuda.synchronize()
+    want = _outs(items)
+    b.set(items, kchunk=kchunk)
+    b.run(ctas_per_sm=ctas, graph=True)
+    torch.cuda.synchronize()
+    b.check()
+    assert b.info()["graph_captures"] == 1
+    for it, w in zip(items, want):
+        for k, v in w.items():
+            assert torch.equal(it[k], v), k
+    fast_only = items[-1:]
+    b.set(fast_only)
+    b.run(ctas_per_sm=ctas, graph=True)
+    b.set(items)
+    b.run(ctas_per_sm=ctas, graph=True)
+    torch.cuda.synchronize()
+    b.check()
+    assert b.info()["graph_captures"] == 2
+    for it, w in zip(items, want):
+        for k, v in w.items():
+            assert torch.equal(it[k], v), k
+    for it in items:
+        for k in KEYS:
+            if it.get(k) is not None:
+                it[k].fill_(-3)
+    lib.batch_project_static(items, kchunk=kchunk, ctas_per_sm=ctas, check=True)
+    for it, w in zip(items, want):
+        for k, v in w.items():
+            assert torch.equal(it[k], v), k

@@ -161,10 +161,13 @@ def test_plain_server_run_loop(ring):
     _check_results(srv.done)
 
 
-def test_geometry_change_while_serving(ring):
+@pytest.mark.parametrize("new_geom", [(45.0, 0.2, 0.115),   # fast kernels
+                                      (35.0, 0.05, 0.1)])   # pixel > step: the general kernel
+def test_geometry_change_while_serving(ring, new_geom):
     """New deskew parameters mid-stream: requests admitted before keep
-    theirs, later ones use the new plans (batches may mix both), and every
-    result equals the plain path with the geometry it was served with."""
+    theirs, later ones use the new plans (batches may mix both, and items of
+    the fast and the general kernel), and every result equals the plain path
+    with the geometry it was served with."""
     from paper_2211_00645_gb300.serve import LiveViewServer, PlanCache, Request
     srv = LiveViewServer(PlanCache(*GEOM), 256 << 20, max_items=16, max_units=1 << 16, result_bytes=64 << 20)
     reqs = []
@@ -182,7 +185,7 @@ def test_geometry_change_while_serving(ring):
         if all(r.ring is None for r in reqs):     # ring ranges returned
             break
     assert all(r.ring is None for r in reqs)
-    srv.set_geometry(45.0, 0.2, 0.115)
+    srv.set_geometry(*new_geom)
     for i, shp in enumerate(SHAPES):
         submit(10 + i, shp)
     srv.run(len(reqs), timeout_s=60)
@@ -190,7 +193,7 @@ def test_geometry_change_while_serving(ring):
     assert len(srv.done) == len(reqs) and ring.in_use() == 0
     geos = {r.rid: r.geometry for r in srv.done}
     assert all(geos[i] == GEOM for i in range(5))
-    assert all(geos[10 + i] == (45.0, 0.2, 0.115) for i in range(5))
+    assert all(geos[10 + i] == new_geom for i in range(5))
     _check_results(srv.done)
 
 

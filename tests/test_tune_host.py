@@ -1,9 +1,11 @@
-"""Autotuner table logic without a GPU: signatures, choice of the fastest
-candidate, ties, caching and the JSON round trip."""
+"""Autotuner table logic without a GPU: signatures, the kernel shapes that
+apply to a batch, choice of the fastest candidate, ties, caching and the
+JSON round trip."""
 import json
 import types
 
-from paper_2211_00645_gb300.tune import Tuner, candidates, signature
+from paper_2211_00645_gb300.tune import (FAST_J8X4, GEN_J8X4, PER_J16X2, PER_J32X2, Tuner, candidates, shapes_for,
+                                         signature)
 
 
 def _items(*shapes, geo=(35.0, 0.3, 0.1)):
@@ -25,25 +27,53 @@ def test_signature_classes():
     assert signature(a, 152) != signature(a, 148)
 
 
+def test_shapes_for_items():
+    """Periodic shapes only when every fast-kernel item shares one family;
+    items with z-sum or arg-max outputs do not count (the general kernel
+    takes them whatever the shape)."""
+    paths = {"per13": (2, 1, 3), "per14": (2, 1, 4), "fast": (1, 0, 0), "gen": (0, 0, 0)}
+
+    def items(*kinds, zsum=()):
+        return [{"plan": k, **({"zsum": 1} if i in zsum else {})} for i, k in enumerate(kinds)]
+
+    def f(its):
+        return shapes_for(its, path_of=lambda p: paths[p])
+
+    both = (PER_J32X2, PER_J16X2, FAST_J8X4, GEN_J8X4)
+    assert f(items("per13", "per13", "gen")) == both
+    assert f(items("per13", "per14")) == (FAST_J8X4, GEN_J8X4)
+    assert f(items("per13", "fast")) == (FAST_J8X4, GEN_J8X4)
+    assert f(items("per13", "fast", zsum=(1,))) == both
+    assert f(items("gen")) == (FAST_J8X4, GEN_J8X4)
+
+
+def test_candidates_per_shape():
+    c = candidates((16, 64), (2, 3, 4), (PER_J32X2, GEN_J8X4))
+    assert c == [(PER_J32X2, 16, 2), (PER_J32X2, 16, 3), (PER_J32X2, 16, 4), (PER_J32X2, 64, 2),
+                 (PER_J32X2, 64, 3), (PER_J32X2, 64, 4), (GEN_J8X4, 16, 2)]
+
+
 def test_tune_picks_fastest_and_caches(tmp_path):
     calls = []
 
-    def timer(k, c):
-        calls.append((k, c))
-        return 100.0 + abs(k - 64) + 10 * abs(c - 3)
+    def timer(sh, k, c):
+        calls.append((sh, k, c))
+        return 100.0 + abs(k - 64) + 10 * abs(c - 3) + (0 if sh == PER_J16X2 else 5)
 
     path = str(tmp_path / "tune.json")
     t = Tuner(path)
     items = _items((100, 256, 512))
-    e = t.tune(items, timer=timer, sm_count=152)
-    assert (e["kchunk"], e["ctas_per_sm"]) == (64, 3)
-    assert len(calls) == len(candidates())
-    assert t.best(items, 152) == (64, 3)
+    shapes = (PER_J32X2, PER_J16X2, FAST_J8X4, GEN_J8X4)
+    e = t.tune(items, timer=timer, sm_count=152, shapes=shapes)
+    assert (e["shape"], e["kchunk"], e["ctas_per_sm"]) == ("per_j16x2", 64, 3)
+    assert len(calls) == len(candidates(shapes=shapes)) == 3 * 15 + 1
+    assert "gen_j8x4/16x2" in e["candidates"] and "per_j32x2/64x3" in e["candidates"]
+    assert t.best(items, 152) == (PER_J16X2, 64, 3)
     calls.clear()
-    t.tune(items, timer=timer, sm_count=152)                  # cached: no timing
+    t.tune(items, timer=timer, sm_count=152, shapes=shapes)   # cached: no timing
     assert not calls
     t2 = Tuner(path)                                           # JSON round trip
-    assert t2.best(items, 152) == (64, 3)
+    assert t2.best(items, 152) == (PER_J16X2, 64, 3)
     with open(path) as f:
         assert signature(items, 152) in json.load(f)
     assert t2.best(_items((400, 1024, 2048)), 152) is None
@@ -51,5 +81,6 @@ def test_tune_picks_fastest_and_caches(tmp_path):
 
 def test_ties_break_to_the_smaller_candidate():
     t = Tuner()
-    e = t.record("x", {(128, 4): 10.0, (32, 2): 10.0, (64, 3): 11.0})
-    assert (e["kchunk"], e["ctas_per_sm"]) == (32, 2)
+    e = t.record("x", {(FAST_J8X4, 128, 4): 10.0, (FAST_J8X4, 32, 2): 10.0, (PER_J32X2, 16, 2): 10.0,
+                       (FAST_J8X4, 64, 3): 11.0})
+    assert (e["shape"], e["kchunk"], e["ctas_per_sm"]) == ("fast_j8x4", 32, 2)

@@ -60,6 +60,8 @@ NCU_TRAFFIC = {
     "volume_f32": {"src_sha": "5705b486b8b8", "bytes_per_launch": 4621428174},
 }
 
+L2_BYTES = 129 * 10**6  # L2 of the GB300 (bytes)
+
 
 def _tree_sha():
     """Hash of every library source and header (identifies the build measured)."""
@@ -256,12 +258,15 @@ def tune_serving(torch, plans, ring):
     return e
 
 
-def adjoint_bench(torch, opm, peak):
+def adjoint_bench(torch, opm, peak, shape=None):
     """Forward deskew, skew adjoint and z-MIP backward (FP32) on the
     differentiable workload 128 x 256 x 256 (theta 30, step 0.4, pixel
-    0.115), each timed with CUDA events against its algorithmic bytes."""
+    0.115; ``shape`` = (nscan, nrows, ncols) replaces its size), each launch
+    timed alone with CUDA events after a write of twice the L2 size, against
+    its algorithmic bytes."""
     c = opm_synth.CONFIGS["diff_128x256x256"]
-    p = opm.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    n, rows, cols = shape or (c.nscan, c.nrows, c.ncols)
+    p = opm.Plan(n, rows, cols, c.theta_deg, c.step, c.pixel)
     s = torch.cuda.current_stream()
     g = torch.Generator(device="cuda").manual_seed(1)
     x = torch.randn(p.raw_shape, generator=g, device="cuda")
@@ -269,24 +274,27 @@ def adjoint_bench(torch, opm, peak):
     r = torch.empty(p.raw_shape, device="cuda")
     gz = torch.randn((p.ny, p.nx), generator=g, device="cuda")
     argz = torch.randint(0, p.nz, (p.ny, p.nx), generator=g, device="cuda", dtype=torch.int32)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
     raw_b, vol_b = 4 * x.numel(), 4 * v.numel()
     calls = {
         "forward_f32": (lambda: opm.opm_deskew(p, x, v, s), raw_b + vol_b),
         "skew_adjoint_f32": (lambda: opm.opm_skew_adjoint(p, v, r, s), vol_b + raw_b),
         "mip_backward": (lambda: opm.opm_mip_backward(p, gz, argz, r, s), 8 * gz.numel() + raw_b),
     }
-    out = {"workload": "diff_128x256x256", "grid": [p.nz, p.ny, p.nx]}
+    out = {"workload": f"diff_{n}x{rows}x{cols}", "grid": [p.nz, p.ny, p.nx],
+           "timing": "each launch alone, after writing 2 x L2 bytes"}
+    reps = 20
     for name, (fn, nbytes) in calls.items():
         for _ in range(3):
             fn()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(50):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in ev:
+            flush.fill_(1)
+            e0.record(s)
             fn()
-        e1.record(s)
+            e1.record(s)
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 50 * 1e-3
+        t = sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps * 1e-3
         out[name] = {"bytes": nbytes, "us": round(t * 1e6, 2), "GBps": round(nbytes / t / 1e9, 1),
                      "frac": round(nbytes / t / 1e9 / peak, 4)}
     return out
@@ -546,6 +554,8 @@ def main():
     ap.add_argument("--serve-fps", type=float, default=2000.0, help="camera frame rate of the paced phase")
     ap.add_argument("--nscan", type=int, default=0,
                     help="scan planes of the live-view stack (0: the workload's 200; smaller for profiler captures)")
+    ap.add_argument("--diff-shape", default="",
+                    help="nscan,nrows,ncols of the differentiable section (default 128,256,256)")
     ap.add_argument("--only", default="all",
                     help="comma list of the sections run after the live-view step: volume, sheet, "
                          "differentiable, rolling, large, serving, cpu (or all, none)")
@@ -741,7 +751,8 @@ def main():
     if "sheet" in only:
         line["sheet_view"] = sheet_bench(torch, opm, cfg, raw, stream, peak)
     if "differentiable" in only:
-        line["differentiable"] = adjoint_bench(torch, opm, peak)
+        dshape = tuple(int(v) for v in args.diff_shape.split(",")) if args.diff_shape else None
+        line["differentiable"] = adjoint_bench(torch, opm, peak, dshape)
     if "rolling" in only:
         line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
     if "large" in only and not args.no_large:

@@ -297,6 +297,30 @@ def test_mip_backward_collisions(lib, shape):
     assert_close(got, ref, what=f"mip backward {shape}")
 
 
+@pytest.mark.parametrize("shape,interp", [(SHAPES[0], 0), (SHAPES[4], 1), (SHAPES[5], 0),
+                                          ((24, 6, 203, 30.0, 0.4, 0.115), 0)])
+def test_mip_backward_is_the_adjoint_of_the_argmax_volume(lib, shape, interp):
+    """The z-MIP backward equals the skew adjoint applied to the volume that
+    holds g[j][x] at (argz[j][x], j, x) and zero elsewhere, bit for bit: both
+    sum each raw sample's terms in ascending j with the same weights, and a
+    zero term leaves a sum unchanged.  Arg-max rows are arbitrary (long runs
+    of one row, out-of-range rows included) and g has signed zeros."""
+    g = O.geometry(*shape)
+    rng = np.random.default_rng(31)
+    gz = rng.standard_normal((g.ny, g.nx)).astype(np.float32)
+    gz[rng.random(gz.shape) < 0.05] = -0.0
+    argz = rng.integers(-1, g.nz + 1, size=(g.ny, g.nx)).astype(np.int32)
+    argz[:, :5] = 0
+    plan = lib.Plan(*shape, interp=interp)
+    G = lib.mip_backward(plan, to_dev(gz, torch), to_dev(argz, torch))
+    vol = np.zeros((g.nz, g.ny, g.nx), np.float32)
+    jj, xx = np.nonzero((argz >= 0) & (argz < g.nz))
+    vol[argz[jj, xx], jj, xx] = gz[jj, xx]
+    A = lib.skew_adjoint(plan, to_dev(vol, torch))
+    torch.cuda.synchronize()
+    assert torch.equal(G, A)
+
+
 def test_non_default_stream_and_no_allocation(lib):
     shape = SHAPES[0]
     R = _stack(shape)

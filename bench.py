@@ -42,8 +42,9 @@ UNIT = "GB/s"
 # Sources each timed kernel is compiled from: a change to any of them voids
 # the stored ncu traffic figure.
 KERNEL_SOURCES = {
-    "periodic": ["csrc/opm_project.cu", "csrc/opm_periodic.cuh", "csrc/opm_tma.cuh", "csrc/opm_common.cuh",
-                 "csrc/opm_internal.h", "csrc/opm_sched.h", "csrc/opm_plan.cu", "../include/opm.h"],
+    "periodic": ["csrc/opm_project.cu", "csrc/opm_periodic.cuh", "csrc/opm_gen.cuh", "csrc/opm_tma.cuh",
+                 "csrc/opm_common.cuh", "csrc/opm_internal.h", "csrc/opm_sched.h", "csrc/opm_plan.cu",
+                 "../include/opm.h"],
     "liveview": ["csrc/opm_project.cu", "csrc/opm_tma.cuh", "csrc/opm_common.cuh", "csrc/opm_internal.h",
                  "csrc/opm_sched.h", "csrc/opm_plan.cu", "../include/opm.h"],
     "volume_f32": ["csrc/opm_deskew.cu", "csrc/opm_common.cuh", "csrc/opm_internal.h", "csrc/opm_sched.h",
@@ -52,12 +53,14 @@ KERNEL_SOURCES = {
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per full-size
 # launch from ncu captures, keyed by the hash of the kernel's sources at
-# capture time (reported as null once a source has changed).  volume_f32:
-# captured with 100 scan planes (213.03 MB read, 2962.64 MB written) and
+# capture time (reported as null once a source has changed).  periodic:
+# captured at full size (448.98 MB read, 9.33 MB written).  volume_f32:
+# captured with 100 scan planes (213.11 MB read, 2963.51 MB written) and
 # scaled to 200 planes, reads by the raw bytes (x2.0) and writes by the
 # volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "volume_f32": {"src_sha": "5705b486b8b8", "bytes_per_launch": 4621428174},
+    "periodic": {"src_sha": "b7f470d083c8", "bytes_per_launch": 458307584},
+    "volume_f32": {"src_sha": "1ea698c7952c", "bytes_per_launch": 4622836946},
 }
 
 L2_BYTES = 129 * 10**6  # L2 of the GB300 (bytes)
@@ -256,6 +259,55 @@ def tune_serving(torch, plans, ring):
     del items, keep
     torch.cuda.empty_cache()
     return e
+
+
+def batch_bench(torch, opm, fixed=None):
+    """One tick of the batched server on device-resident inputs: the six
+    stacks of the serving mix (seeded shapes; uniform random uint16 made on
+    the device), each channel an item of one batch, z-MIP + y-MIP.  The
+    autotuner times every kernel shape x kchunk x CTAs-per-SM candidate and
+    keeps the fastest; ``fixed`` = (shape name, kchunk, ctas) times that
+    configuration alone instead (profiler captures)."""
+    from paper_2211_00645_gb300.tune import SHAPE_IDS, Tuner
+    plans = {}
+    items, keep = [], []
+    g = torch.Generator(device="cuda").manual_seed(11)
+    for (n, r, c, C) in opm_synth.serve_shapes(6, seed=11):
+        plan = plans.setdefault((n, r, c), opm.Plan(n, r, c, 35.0, 0.3, 0.1))
+        raw = torch.randint(0, 4096, (n, r, c * C), generator=g, device="cuda", dtype=torch.int32)
+        raw = raw.to(torch.int16).view(torch.uint16)
+        keep.append(raw)
+        for ch in range(C):
+            items.append({"plan": plan, "raw": raw[:, :, ch * c:], "row_pitch": C * c, "plane_pitch": r * C * c,
+                          "zmip": torch.empty((plan.ny, plan.nx), device="cuda"),
+                          "ymip": torch.empty((plan.nz, plan.nx), device="cuda")})
+    raw_b = sum(2 * k.numel() for k in keep)
+    out = {"workload": "serving mix: 6 stacks, 2 channels each (theta 35, step 0.3, pixel 0.1), "
+                       "z-MIP + y-MIP per channel, one batch", "items": len(items), "raw_bytes": raw_b}
+    if fixed:
+        shape, kchunk, ctas = fixed
+        b = opm.Batch(max_items=len(items), max_units=1 << 24)
+        b.set(items, kchunk, SHAPE_IDS[shape])
+        b.upload()
+        s = torch.cuda.current_stream()
+        for _ in range(3):
+            b.launch(ctas, s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(10):
+            b.launch(ctas, s)
+        e1.record(s)
+        e1.synchronize()
+        out["fixed"] = {"shape": shape, "kchunk": kchunk, "ctas_per_sm": ctas,
+                        "us": round(e0.elapsed_time(e1) * 100, 2)}
+    else:
+        e = Tuner().tune(items, reps=5, warmup=2)
+        out["tuned"] = {k: e[k] for k in ("shape", "kchunk", "ctas_per_sm", "us")}
+        out["candidates_us"] = e["candidates"]
+        out["tuned"]["GBps_raw"] = round(raw_b / (e["us"] * 1e-6) / 1e9, 1)
+    del items, keep
+    torch.cuda.empty_cache()
+    return out
 
 
 def adjoint_bench(torch, opm, peak, shape=None):
@@ -558,9 +610,11 @@ def main():
                     help="nscan,nrows,ncols of the differentiable section (default 128,256,256)")
     ap.add_argument("--only", default="all",
                     help="comma list of the sections run after the live-view step: volume, sheet, "
-                         "differentiable, rolling, large, serving, cpu (or all, none)")
+                         "differentiable, rolling, large, batch, serving, cpu (or all, none)")
+    ap.add_argument("--batch-config", default="",
+                    help="shape,kchunk,ctas (e.g. per_j32x2,256,4): time that batch configuration instead of tuning")
     args = ap.parse_args()
-    sections = {"volume", "sheet", "differentiable", "rolling", "large", "serving", "cpu"}
+    sections = {"volume", "sheet", "differentiable", "rolling", "large", "batch", "serving", "cpu"}
     only = sections if args.only == "all" else set() if args.only == "none" else set(args.only.split(","))
     if only - sections:
         ap.error(f"unknown sections {sorted(only - sections)}")
@@ -597,7 +651,8 @@ def main():
     raw.view(torch.int16).copy_(host_raw)
     zmip = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
     ymip = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
-    vol = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
+    # the FP32 volume only for the volume section (the step never writes one)
+    vol = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev) if "volume" in only else None
     host_z = torch.empty((plan.ny, plan.nx), dtype=torch.float32).pin_memory()
     host_y = torch.empty((plan.nz, plan.nx), dtype=torch.float32).pin_memory()
     stream = torch.cuda.current_stream()
@@ -608,8 +663,9 @@ def main():
 
     for _ in range(args.warmup):
         step()
-        opm.opm_deskew(plan, raw, vol, stream)
-        opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+        if vol is not None:
+            opm.opm_deskew(plan, raw, vol, stream)
+            opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
     torch.cuda.synchronize()
     opm.opm_plan_check(plan)
 
@@ -634,19 +690,21 @@ def main():
 
     # ---- the separate full FP32 volume run of the same stack: the volume alone,
     # and volume + live view from one opm_deskew_mip call (side by side)
-    KV = max(20, K // 8) if "volume" in only else 1
-    v0, v1, v2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    v0.record(stream)
-    for _ in range(KV):
-        opm.opm_deskew(plan, raw, vol, stream)
-    v1.record(stream)
-    for _ in range(KV):
-        opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
-    v2.record(stream)
-    torch.cuda.synchronize()
-    t_vol = v0.elapsed_time(v1) / KV * 1e-3
-    t_pair = v1.elapsed_time(v2) / KV * 1e-3
-    opm.opm_plan_check(plan)
+    t_vol = t_pair = None
+    if vol is not None:
+        KV = max(20, K // 8)
+        v0, v1, v2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        v0.record(stream)
+        for _ in range(KV):
+            opm.opm_deskew(plan, raw, vol, stream)
+        v1.record(stream)
+        for _ in range(KV):
+            opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+        v2.record(stream)
+        torch.cuda.synchronize()
+        t_vol = v0.elapsed_time(v1) / KV * 1e-3
+        t_pair = v1.elapsed_time(v2) / KV * 1e-3
+        opm.opm_plan_check(plan)
     opm.opm_plan_check(plan)
 
     # ---- end to end through the C ABI: every step copies its stack in from
@@ -704,7 +762,8 @@ def main():
     path = opm.opm_plan_path(plan)
     kname = {opm.OPM_PATH_PERIODIC: "periodic", opm.OPM_PATH_FAST: "liveview"}.get(path[0], "liveview_general")
     tr = NCU_TRAFFIC.get(kname)
-    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(kname) else None
+    full_size = args.nscan in (0, 200)  # the captured traffic is that of the full 200-plane launch
+    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(kname) and full_size else None
     ach = live_b / (ms_step * 1e-3) / 1e9
     pair_b = live_b + vol_b
     line = {
@@ -733,21 +792,19 @@ def main():
         "clocks": clocks,
     }
     vtr = NCU_TRAFFIC.get("volume_f32")
-    line["volume"] = {
-        "what": "the separate full FP32 volume run of the same stack (512 x 1021 x 2048)",
-        "deskew_f32": {"bytes": vol_b, "us": round(t_vol * 1e6, 2), "GBps": round(vol_b / t_vol / 1e9, 1),
-                       "frac": round(vol_b / t_vol / 1e9 / peak, 4), "volumes_per_s": round(1.0 / t_vol, 1),
-                       "traffic": vtr["bytes_per_launch"] if vtr and vtr["src_sha"] == _src_sha("volume_f32") else None},
-        "deskew_mip_side_by_side": {"call": "opm_deskew_mip (volume + live view, the two kernels side by side)",
-                                    "bytes": pair_b, "us": round(t_pair * 1e6, 2),
-                                    "GBps": round(pair_b / t_pair / 1e9, 1),
-                                    "frac": round(pair_b / t_pair / 1e9 / peak, 4)},
-    }
-    if "volume" not in only:
-        del line["volume"]
-    else:
-        line["volume"]["one_pass_fused"] = one_pass(torch, opm, cfg, raw, vol, zmip, ymip, stream, vol_b, live_b,
-                                                    peak)
+    if vol is not None:
+        line["volume"] = {
+            "what": "the separate full FP32 volume run of the same stack (512 x 1021 x 2048)",
+            "deskew_f32": {"bytes": vol_b, "us": round(t_vol * 1e6, 2), "GBps": round(vol_b / t_vol / 1e9, 1),
+                           "frac": round(vol_b / t_vol / 1e9 / peak, 4), "volumes_per_s": round(1.0 / t_vol, 1),
+                           "traffic": (vtr["bytes_per_launch"] if vtr and vtr["src_sha"] == _src_sha("volume_f32")
+                                       and full_size else None)},
+            "deskew_mip_side_by_side": {"call": "opm_deskew_mip (volume + live view, the two kernels side by side)",
+                                        "bytes": pair_b, "us": round(t_pair * 1e6, 2),
+                                        "GBps": round(pair_b / t_pair / 1e9, 1),
+                                        "frac": round(pair_b / t_pair / 1e9 / peak, 4)},
+            "one_pass_fused": one_pass(torch, opm, cfg, raw, vol, zmip, ymip, stream, vol_b, live_b, peak),
+        }
     if "sheet" in only:
         line["sheet_view"] = sheet_bench(torch, opm, cfg, raw, stream, peak)
     if "differentiable" in only:
@@ -757,6 +814,9 @@ def main():
         line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
     if "large" in only and not args.no_large:
         line["large_volume"] = large_bench(torch, opm, peak)
+    if "batch" in only:
+        bc = args.batch_config.split(",") if args.batch_config else None
+        line["batch"] = batch_bench(torch, opm, (bc[0], int(bc[1]), int(bc[2])) if bc else None)
     if "serving" in only:
         del vol, raw
         torch.cuda.empty_cache()

@@ -54,12 +54,13 @@ KERNEL_SOURCES = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per full-size
 # launch from ncu captures, keyed by the hash of the kernel's sources at
 # capture time (reported as null once a source has changed).  periodic:
-# captured at full size (448.98 MB read, 9.33 MB written).  volume_f32:
+# captured at full size (448.98 MB read, 9.33 MB written; 76.8 M warp
+# instructions from the full-size --set full capture).  volume_f32:
 # captured with 100 scan planes (213.11 MB read, 2963.51 MB written) and
 # scaled to 200 planes, reads by the raw bytes (x2.0) and writes by the
 # volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "periodic": {"src_sha": "b7f470d083c8", "bytes_per_launch": 458307584},
+    "periodic": {"src_sha": "b7f470d083c8", "bytes_per_launch": 458307584, "warp_insts_per_launch": 76816260},
     "volume_f32": {"src_sha": "1ea698c7952c", "bytes_per_launch": 4622836946},
 }
 
@@ -82,6 +83,22 @@ def _src_sha(kernel):
         with open(os.path.normpath(os.path.join(ROOT, "paper_2211_00645_gb300", rel)), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
+
+
+# Derived issue peak: one warp instruction per scheduler per cycle at the
+# maximum SM clock (152 SMs x 4 schedulers x 2.07 GHz).
+ISSUE_PEAK = 152 * 4 * 2.07e9
+
+
+def issue_bound(tr, ms_step):
+    """The step against the instruction-issue roofline (the fused path may be
+    issue-bound): ncu's warp instructions per launch over the derived issue
+    peak, as a time floor and a fraction of the measured time."""
+    if not tr or "warp_insts_per_launch" not in tr:
+        return None
+    floor_us = tr["warp_insts_per_launch"] / ISSUE_PEAK * 1e6
+    return {"warp_insts_per_launch": tr["warp_insts_per_launch"], "peak_warp_insts_per_s": ISSUE_PEAK,
+            "floor_us": round(floor_us, 2), "frac": round(floor_us / (ms_step * 1e3), 4)}
 
 
 def peaks():
@@ -792,7 +809,8 @@ def main():
                      "frac": round(ach / peak, 4), "traffic": traffic,
                      "kernel": f"k_project_{'per' if kname == 'periodic' else 'fast'} + k_init_outputs "
                                "(one opm_project call, timed together)",
-                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "issue": issue_bound(tr if traffic is not None else None, ms_step)},
         "e2e": {"value": round(ws * live_b / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(host_raw.numel() * 2),
                 "d2h_bytes_per_step": int((host_z.numel() + host_y.numel()) * 4),

@@ -405,6 +405,22 @@ def test_liveview_full_size_sampled(lib, liveview):
     assert np.max(np.abs(got - ref)) <= TOL * float(np.max(np.abs(zmip)))
 
 
+def test_liveview_full_size_every_column(lib, liveview):
+    """The live view of the full 200 x 512 x 2048 stack (the bench's step,
+    periodic kernel) against the oracle on every column, the oracle run over
+    blocks of columns on all host cores."""
+    from oracle_pool import project_columns
+    c, R = liveview
+    plan = lib.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    assert lib.opm_plan_path(plan)[0] == lib.OPM_PATH_PERIODIC
+    out = lib.project(plan, to_dev(R, torch), zmip=True, ymip=True)
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    zmip, ymip = project_columns(R, c.theta_deg, c.step, c.pixel)
+    assert_close(out["zmip"].cpu().numpy(), zmip, what="zmip, every column")
+    assert_close(out["ymip"].cpu().numpy(), ymip, what="ymip, every column")
+
+
 def test_large_full_size_sampled(lib):
     """1000 x 1024 x 2048 uint16 stack (theta 45, step 0.2, pixel 0.115):
     FP32 and round-to-nearest uint16 volumes and the z-MIP at full size,

@@ -629,7 +629,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-saturated", type=int, default=1800, help="stacks arriving at once (0: skip)")
     ap.add_argument("--serve-budget-gb", type=int, default=40)
-    ap.add_argument("--serve-ring-gb", type=int, default=8)
+    ap.add_argument("--serve-ring-gb", type=int, default=16,
+                    help="pinned host ring of the camera (8 GB stalls acquisitions at 20 stacks/s)")
     ap.add_argument("--serve-fps", type=float, default=2000.0, help="camera frame rate of the paced phase")
     ap.add_argument("--nscan", type=int, default=0,
                     help="scan planes of the live-view stack (0: the workload's 200; smaller for profiler captures)")

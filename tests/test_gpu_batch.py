@@ -7,7 +7,7 @@ import pytest
 
 import opm_synth
 import oracle as O
-from gpu_util import TOL, assert_close, check_argz, to_dev
+from gpu_util import TOL, assert_between, assert_close, check_argz, nearest_bounds, to_dev
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -279,3 +279,36 @@ def test_general_items_graph_static_and_tunables(lib, kchunk, ctas):
     for it, w in zip(items, want):
         for k, v in w.items():
             assert torch.equal(it[k], v), k
+
+
+def test_general_and_fast_items_nearest(lib):
+    """NEAREST plans in one batch: general items (pixel > step, ny < 32, z-sum)
+    and a fast item equal their stand-alone calls bit for bit, and lie within
+    the oracle's bounds at half-plane ties."""
+    shapes = [((16, 20, 64, 35.0, 0.05, 0.1), ("zmip", "ymip", "zsum")),
+              ((6, 10, 136, 35.0, 0.3, 0.1), ("zmip", "ymip")),
+              ((64, 128, 128, 30.0, 0.4, 0.115), ("zmip", "ymip"))]
+    items, refs = [], []
+    for i, (shape, keys) in enumerate(shapes):
+        R = _stack(shape, 80 + i)
+        plan = lib.Plan(*shape, interp=lib.OPM_INTERP_NEAREST)
+        it = {"plan": plan, "raw": to_dev(R, torch)}
+        for k in keys:
+            it[k] = torch.full((plan.nz if k == "ymip" else plan.ny, plan.nx), -7.0, device="cuda")
+        items.append(it)
+        refs.append((shape, R, keys))
+    b = lib.Batch(max_items=4)
+    b.set(items)
+    b.run()
+    torch.cuda.synchronize()
+    b.check()
+    for it, (shape, R, keys) in zip(items, refs):
+        single = lib.project(it["plan"], to_dev(R, torch), **{k: k in keys for k in KEYS})
+        for k in keys:
+            assert torch.equal(it[k], single[k]), (shape, k)
+        g = O.geometry(*shape)
+        lo, hi = nearest_bounds(R, g, O)
+        assert_between(it["zmip"].cpu().numpy(), lo.max(0), hi.max(0), what=f"zmip nearest {shape}")
+        assert_between(it["ymip"].cpu().numpy(), lo.max(1), hi.max(1), what=f"ymip nearest {shape}")
+        if "zsum" in keys:
+            assert_between(it["zsum"].cpu().numpy(), lo.sum(0), hi.sum(0), what=f"zsum nearest {shape}")

@@ -1,25 +1,33 @@
-// Batched live view: one persistent launch of the fast projection over many
-// stacks, channels and ROIs of uneven sizes.
+// Batched live view: persistent launches of the projection kernels over
+// many stacks, channels and ROIs of uneven sizes.
 //
 // The host turns every item into a TMA descriptor (its raw pointer and
-// pitches, so a channel can be a strided ROI of a shared frame stack) and
-// every item's (x-tile, j-tile, row chunk) into a work unit.  Units are
-// sorted by decreasing length and dealt round-robin to a grid of
-// ctas_per_sm x SM persistent CTAs; each CTA runs the fast kernel's producer
-// and consumer loops unit after unit on one mbarrier ring whose stage counter
+// pitches, so a channel can be a strided ROI of a shared frame stack) and its
+// tiles into work units.  Items the fast kernels take (a fast-eligible plan,
+// z-MIP / y-MIP only) get one unit per (x-tile, j-tile, row chunk); all other
+// items (pixel > step, ny < 32, z-sum or arg-max outputs) get one unit per
+// (x-tile, j-tile) and whole row band, for the general kernel.  Each kind of
+// unit is sorted by decreasing length and dealt onto balanced lists, one per
+// persistent CTA of its kernel.  A CTA runs its kernel's producer and
+// consumer loops unit after unit on one mbarrier ring whose stage counter
 // carries on across units, so the next unit's slabs stream in while the
-// current one drains.
+// current one drains.  The fast items run in the kernel shape the caller
+// picks (opm_shape: periodic 32 x 2 or 16 x 2, fast 8 x 4) or all items in
+// the general kernel; the results are the same in every shape.
 //
 // Work-list image (host staging and device copy share it):
 //   [0, 256)            BatchHdr: unit and output-segment counts and offsets
-//   [256, ...)          BatchItemDev per item (TMA descriptor + outputs)
-//   off_segs            BatchSeg per output to zero (z-MIP, y-MIP)
-//   off_lists           per persistent-CTA list: first unit (n_lists + 1)
-//   off_units           WorkUnit per work unit, list by list (a balanced
-//                       longest-first schedule, computed on the host)
+//   [256, ...)          BatchItemDev per item (TMA descriptor, tables, outputs)
+//   off_segs            BatchSeg per output to zero (y-MIPs, fast items' z-MIPs)
+//   off_lists           per fast-kernel CTA list: first unit (n_lists + 1)
+//   off_glists          per general-kernel CTA list: first unit
+//   off_units           WorkUnit per work unit, list by list (balanced
+//                       longest-first schedules, computed on the host): the
+//                       fast units, then the general ones
 // Only the used prefix is copied per upload.  The kernels read the counts
 // from the header, so a launch captured in a CUDA graph stays valid for any
-// later content with the same slab depth.
+// later content with the same launch shape (kernel shape, slab depths, kinds
+// of items, grids).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 

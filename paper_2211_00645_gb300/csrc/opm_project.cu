@@ -22,7 +22,12 @@
 //  * Only rows whose band can carry non-zero weight for the tile are visited;
 //    all other rows are exactly zero and enter the maxima as the value 0.
 //
-// Two kernels share that structure:
+// Three kernels share that structure:
+//  k_project_per   the periodic kernel (opm_periodic.cuh) for plans whose
+//                  pixel/step is a compiled ratio p/q (1/3): the fast
+//                  kernel's producer and schedule, compute warps of 32
+//                  columns j x 2 columns x per lane with every plane step
+//                  at a compile-time position.
 //  k_project_fast  uint16 input, z-MIP and/or y-MIP, full 32-column tiles of
 //                  plans whose columns never skip a plane (checked on the
 //                  host with the kernel's own arithmetic).  Two rows per stage
@@ -34,7 +39,8 @@
 //                  chunks.
 //  k_project_gen   every output (z-sum, first argmax), uint16 or FP32 input,
 //                  any tile (partial last tile, column steps of several
-//                  planes), one row per stage, whole band per CTA.
+//                  planes), one row per stage, whole band per CTA
+//                  (opm_gen.cuh, shared with the batched general kernel).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 

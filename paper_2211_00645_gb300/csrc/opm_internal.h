@@ -63,7 +63,7 @@ static_assert(sizeof(FastRow) == 288, "FastRow is copied as 288 bytes");
 struct Family {
   int p, q;
 };
-constexpr Family kFamilies[] = {{1, 3}};
+constexpr Family kFamilies[] = {{1, 3}, {1, 2}};
 constexpr int kNumFamilies = (int)(sizeof(kFamilies) / sizeof(kFamilies[0]));
 constexpr int kPerRun = 32;       // columns j per compute warp of the periodic kernel
 constexpr int kPerCtasPerSm = 4;  // its persistent CTAs per SM

@@ -122,11 +122,12 @@ def test_shape_arguments_optional(opm):
 
 def test_plan_path_classification(opm):
     """Which live-view kernel a plan takes is decided on the host: pixel/step
-    = 1/3 plans take the periodic kernel, other pixel <= step plans the fast
-    one, pixel > step plans the general one."""
+    = 1/3 or 1/2 plans take the periodic kernel, other pixel <= step plans
+    the fast one, pixel > step plans the general one."""
     cases = [((200, 512, 2048, 35.0, 0.3, 0.1), (opm.OPM_PATH_PERIODIC, 1, 3)),
              ((33, 50, 200, 60.0, 0.45, 0.15), (opm.OPM_PATH_PERIODIC, 1, 3)),
              ((64, 128, 128, 30.0, 0.4, 0.115), (opm.OPM_PATH_FAST, 0, 0)),
+             ((100, 96, 264, 35.0, 0.2, 0.1), (opm.OPM_PATH_PERIODIC, 1, 2)),
              ((16, 20, 64, 35.0, 0.05, 0.1), (opm.OPM_PATH_GENERAL, 0, 0))]
     for shape, want in cases:
         plan = opm.Plan(*shape)

@@ -126,3 +126,37 @@ def test_periodic_batch_and_mixed_batch(lib):
             torch.cuda.synchronize()
             assert torch.equal(it["zmip"], ref["zmip"]) and torch.equal(it["ymip"], ref["ymip"])
         b.close()
+
+
+# pixel/step = 1/2: the second compiled family
+HALF_SHAPES = [
+    (100, 96, 264, 35.0, 0.2, 0.1),    # ragged x tile
+    (64, 128, 256, 30.0, 0.4, 0.2),
+    (41, 33, 128, 60.0, 0.25, 0.125),  # exact cos 1/2, odd row count
+]
+
+
+@pytest.mark.parametrize("shape", HALF_SHAPES)
+def test_half_family_matches_oracle_fast_kernel_and_batch(lib, monkeypatch, shape):
+    R = _stack(shape, seed=13)
+    plan = lib.Plan(*shape)
+    assert lib.opm_plan_path(plan) == (lib.OPM_PATH_PERIODIC, 1, 2)
+    fast = _fast_plan(lib, monkeypatch, shape)
+    assert lib.opm_plan_path(fast)[0] == lib.OPM_PATH_FAST
+    raw = to_dev(R, torch)
+    a = lib.project(plan, raw, zmip=True, ymip=True)
+    b = lib.project(fast, raw, zmip=True, ymip=True)
+    bt = lib.Batch(max_items=1)
+    item = {"plan": plan, "raw": raw, "zmip": torch.empty_like(a["zmip"]), "ymip": torch.empty_like(a["ymip"])}
+    bt.set([item])
+    assert bt.info()["shape"] == lib.OPM_SHAPE_PER_J32X2
+    bt.run()
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    bt.check()
+    assert torch.equal(a["zmip"], b["zmip"]) and torch.equal(a["ymip"], b["ymip"])
+    assert torch.equal(item["zmip"], a["zmip"]) and torch.equal(item["ymip"], a["ymip"])
+    g = O.geometry(*shape)
+    zmip, _, ymip, _ = O.project(R.astype(np.float64), g)
+    assert_close(a["zmip"].cpu().numpy(), zmip, what="zmip")
+    assert_close(a["ymip"].cpu().numpy(), ymip, what="ymip")

@@ -60,7 +60,7 @@ KERNEL_SOURCES = {
 # scaled to 200 planes, reads by the raw bytes (x2.0) and writes by the
 # volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "periodic": {"src_sha": "6af43abfd84e", "bytes_per_launch": 458307584, "warp_insts_per_launch": 76816260},
+    "periodic": {"src_sha": "7c739f76f346", "bytes_per_launch": 458307584, "warp_insts_per_launch": 76816260},
     "volume_f32": {"src_sha": "1ea698c7952c", "bytes_per_launch": 4622836946},
 }
 

@@ -312,6 +312,7 @@ typedef enum {
                            /* two rows per stage                                          */
   OPM_SHAPE_PER_J32X2 = 2, /* periodic kernel: 32 columns j per warp x 2 x per lane      */
   OPM_SHAPE_PER_J16X2 = 3, /* periodic kernel: 16 columns j per warp x 2 x per lane      */
+                           /* (family 1/3; other families run as PER_J32X2)              */
   OPM_SHAPE_GEN_J8X4 = 4   /* general kernel for every item: 8 j x 4 x, whole row band   */
                            /* per unit, one row per stage                                 */
 } opm_shape;

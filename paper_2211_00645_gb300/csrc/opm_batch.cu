@@ -466,6 +466,8 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
   out->family = family;
   out->n_gunits = ngen;
   out->Pg = Pg;
+  // 16-column runs exist for the first family only; the others run 32
+  if (shape == OPM_SHAPE_PER_J16X2 && family != 1) shape = OPM_SHAPE_PER_J32X2;
   out->run = shape == OPM_SHAPE_PER_J16X2 ? 16 : kPerRun;
   out->shape = shape;
   return OPM_OK;
@@ -481,10 +483,13 @@ void launch_batch_per(const unsigned char* dev_wl, const WorkList& wl, int grid,
     if (wl.family - 1 != F) return launch_batch_per<F + 1>(dev_wl, wl, grid, err, s);
     constexpr int Pp = kFamilies[F].p, Qq = kFamilies[F].q;
     const size_t smem = batch_smem(wl.Pl, wl.family);
-    if (wl.run == 16)
-      k_batch_per<Pp, Qq, 16><<<grid, per::Cfg<16>::kThreads, smem, s>>>(dev_wl, wl.Pl, err);
-    else
-      k_batch_per<Pp, Qq, kPerRun><<<grid, per::Cfg<kPerRun>::kThreads, smem, s>>>(dev_wl, wl.Pl, err);
+    if constexpr (F == 0) {  // 16-column runs are compiled for the first family only
+      if (wl.run == 16) {
+        k_batch_per<Pp, Qq, 16><<<grid, per::Cfg<16>::kThreads, smem, s>>>(dev_wl, wl.Pl, err);
+        return;
+      }
+    }
+    k_batch_per<Pp, Qq, kPerRun><<<grid, per::Cfg<kPerRun>::kThreads, smem, s>>>(dev_wl, wl.Pl, err);
   }
 }
 
@@ -542,7 +547,8 @@ template <int F>
 cudaError_t set_per_attrs(int smem_optin) {
   if constexpr (F < kNumFamilies) {
     cudaError_t e = set_kernel_smem(k_batch_per<kFamilies[F].p, kFamilies[F].q, kPerRun>, smem_optin);
-    if (e == cudaSuccess) e = set_kernel_smem(k_batch_per<kFamilies[F].p, kFamilies[F].q, 16>, smem_optin);
+    if constexpr (F == 0)
+      if (e == cudaSuccess) e = set_kernel_smem(k_batch_per<kFamilies[F].p, kFamilies[F].q, 16>, smem_optin);
     return e == cudaSuccess ? set_per_attrs<F + 1>(smem_optin) : e;
   }
   return cudaSuccess;

@@ -44,8 +44,9 @@ SHAPE_IDS = {v: k for k, v in SHAPE_NAMES.items()}
 
 def shapes_for(items, path_of: Optional[Callable] = None) -> Tuple[int, ...]:
     """Kernel shapes that apply to ``items``: the periodic ones when every
-    item the fast kernels take shares one periodic family, the fast one, and
-    the general one (which takes any item)."""
+    item the fast kernels take shares one periodic family (16-column runs
+    for the 1/3 family only), the fast one, and the general one (which takes
+    any item)."""
     if path_of is None:
         from . import opm_plan_path as path_of
     fams = set()
@@ -62,7 +63,9 @@ def shapes_for(items, path_of: Optional[Callable] = None) -> Tuple[int, ...]:
             fast = True
     out = []
     if fast and len(fams) == 1 and None not in fams:
-        out += [PER_J32X2, PER_J16X2]
+        out += [PER_J32X2]
+        if fams == {(1, 3)}:        # 16-column runs are compiled for the 1/3 family only
+            out += [PER_J16X2]
     return tuple(out + [FAST_J8X4, GEN_J8X4])
 
 

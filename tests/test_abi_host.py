@@ -128,6 +128,7 @@ def test_plan_path_classification(opm):
              ((33, 50, 200, 60.0, 0.45, 0.15), (opm.OPM_PATH_PERIODIC, 1, 3)),
              ((64, 128, 128, 30.0, 0.4, 0.115), (opm.OPM_PATH_FAST, 0, 0)),
              ((100, 96, 264, 35.0, 0.2, 0.1), (opm.OPM_PATH_PERIODIC, 1, 2)),
+             ((100, 96, 264, 35.0, 0.15, 0.1), (opm.OPM_PATH_FAST, 0, 0)),
              ((16, 20, 64, 35.0, 0.05, 0.1), (opm.OPM_PATH_GENERAL, 0, 0))]
     for shape, want in cases:
         plan = opm.Plan(*shape)

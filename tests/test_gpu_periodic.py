@@ -1,6 +1,6 @@
-"""The periodic live-view kernel: plans whose pixel/step is 1/3 step through
-their staged planes in one of three patterns per 32-column tile row and run
-straight-line code per pattern.  It must reproduce the FP64 oracle within the
+"""The periodic live-view kernel: plans whose pixel/step is a compiled ratio
+p/q (1/3, 1/2) step through their staged planes in one of q patterns per
+32-column tile row and run straight-line code per pattern.  It must reproduce the FP64 oracle within the
 bound, the fast kernel (same plan made with OPM_NO_PERIODIC=1) bit for bit,
 the maxima of the deskewed volume bit for bit, and the batched path."""
 import numpy as np
@@ -128,19 +128,19 @@ def test_periodic_batch_and_mixed_batch(lib):
         b.close()
 
 
-# pixel/step = 1/2: the second compiled family
-HALF_SHAPES = [
-    (100, 96, 264, 35.0, 0.2, 0.1),    # ragged x tile
-    (64, 128, 256, 30.0, 0.4, 0.2),
-    (41, 33, 128, 60.0, 0.25, 0.125),  # exact cos 1/2, odd row count
+# the other compiled family: pixel/step = 1/2
+FAMILY_SHAPES = [
+    ((100, 96, 264, 35.0, 0.2, 0.1), (1, 2)),    # ragged x tile
+    ((64, 128, 256, 30.0, 0.4, 0.2), (1, 2)),
+    ((41, 33, 128, 60.0, 0.25, 0.125), (1, 2)),  # exact cos 1/2, odd row count
 ]
 
 
-@pytest.mark.parametrize("shape", HALF_SHAPES)
-def test_half_family_matches_oracle_fast_kernel_and_batch(lib, monkeypatch, shape):
+@pytest.mark.parametrize("shape,pq", FAMILY_SHAPES)
+def test_other_families_match_oracle_fast_kernel_and_batch(lib, monkeypatch, shape, pq):
     R = _stack(shape, seed=13)
     plan = lib.Plan(*shape)
-    assert lib.opm_plan_path(plan) == (lib.OPM_PATH_PERIODIC, 1, 2)
+    assert lib.opm_plan_path(plan) == (lib.OPM_PATH_PERIODIC, *pq)
     fast = _fast_plan(lib, monkeypatch, shape)
     assert lib.opm_plan_path(fast)[0] == lib.OPM_PATH_FAST
     raw = to_dev(R, torch)
@@ -148,7 +148,7 @@ def test_half_family_matches_oracle_fast_kernel_and_batch(lib, monkeypatch, shap
     b = lib.project(fast, raw, zmip=True, ymip=True)
     bt = lib.Batch(max_items=1)
     item = {"plan": plan, "raw": raw, "zmip": torch.empty_like(a["zmip"]), "ymip": torch.empty_like(a["ymip"])}
-    bt.set([item])
+    bt.set([item], 64, lib.OPM_SHAPE_PER_J16X2)       # 16-column runs fall back to 32 outside 1/3
     assert bt.info()["shape"] == lib.OPM_SHAPE_PER_J32X2
     bt.run()
     torch.cuda.synchronize()

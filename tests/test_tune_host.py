@@ -31,7 +31,7 @@ def test_shapes_for_items():
     """Periodic shapes only when every fast-kernel item shares one family;
     items with z-sum or arg-max outputs do not count (the general kernel
     takes them whatever the shape)."""
-    paths = {"per13": (2, 1, 3), "per14": (2, 1, 4), "fast": (1, 0, 0), "gen": (0, 0, 0)}
+    paths = {"per13": (2, 1, 3), "per14": (2, 1, 4), "per12": (2, 1, 2), "fast": (1, 0, 0), "gen": (0, 0, 0)}
 
     def items(*kinds, zsum=()):
         return [{"plan": k, **({"zsum": 1} if i in zsum else {})} for i, k in enumerate(kinds)]
@@ -45,6 +45,7 @@ def test_shapes_for_items():
     assert f(items("per13", "fast")) == (FAST_J8X4, GEN_J8X4)
     assert f(items("per13", "fast", zsum=(1,))) == both
     assert f(items("gen")) == (FAST_J8X4, GEN_J8X4)
+    assert f(items("per12", "per12")) == (PER_J32X2, FAST_J8X4, GEN_J8X4)   # no 16-column runs for 1/2
 
 
 def test_candidates_per_shape():

@@ -327,6 +327,42 @@ def batch_bench(torch, opm, fixed=None):
     return out
 
 
+def xshard_bench(torch, opm, cfg, raw, stream, t_whole):
+    """The x-column partition of one stack (dist.xshard), measured on one GPU:
+    the live view of one rank's columns for 2, 4 and 8 ranks, against the
+    whole stack's step.  Each rank would run its part on its own GPU with no
+    exchange, so whole / (N x part) is the partition's efficiency before the
+    gather for display."""
+    from paper_2211_00645_gb300 import dist as pdist
+    out = {"what": "live view of rank 0's columns (contiguous copy), timed alone; no collective",
+           "whole_us": round(t_whole * 1e6, 2)}
+    for n in (2, 4, 8):
+        x0, x1 = pdist.xshard(cfg.ncols, 0, n)
+        part = raw[:, :, x0:x1].contiguous()
+        # copies enough that the rotation exceeds twice L2: every launch reads from HBM
+        ncopy = max(2, -(-2 * int(L2_BYTES) // (part.numel() * 2)))
+        parts = [part] + [part.clone() for _ in range(ncopy - 1)]
+        plan = opm.Plan(cfg.nscan, cfg.nrows, x1 - x0, cfg.theta_deg, cfg.step, cfg.pixel)
+        z = torch.empty((plan.ny, plan.nx), device="cuda")
+        y = torch.empty((plan.nz, plan.nx), device="cuda")
+        for i in range(3):
+            opm.opm_project(plan, parts[i % ncopy], z, None, y, None, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10 * ncopy
+        e0.record(stream)
+        for i in range(reps):
+            opm.opm_project(plan, parts[i % ncopy], z, None, y, None, stream)
+        e1.record(stream)
+        e1.synchronize()
+        opm.opm_plan_check(plan)
+        t = e0.elapsed_time(e1) / reps * 1e-3
+        out[f"ranks_{n}"] = {"columns": x1 - x0, "unit_rows": opm.opm_plan_schedule(plan)[2],
+                             "part_us": round(t * 1e6, 2), "copies": ncopy,
+                             "efficiency": round(t_whole / (n * t), 3)}
+        del part, parts, z, y
+    return out
+
+
 def adjoint_bench(torch, opm, peak, shape=None):
     """Forward deskew, skew adjoint and z-MIP backward (FP32) on the
     differentiable workload 128 x 256 x 256 (theta 30, step 0.4, pixel
@@ -638,11 +674,11 @@ def main():
                     help="nscan,nrows,ncols of the differentiable section (default 128,256,256)")
     ap.add_argument("--only", default="all",
                     help="comma list of the sections run after the live-view step: volume, sheet, "
-                         "differentiable, rolling, large, batch, serving, cpu (or all, none)")
+                         "differentiable, rolling, xshard, large, batch, serving, cpu (or all, none)")
     ap.add_argument("--batch-config", default="",
                     help="shape,kchunk,ctas (e.g. per_j32x2,256,4): time that batch configuration instead of tuning")
     args = ap.parse_args()
-    sections = {"volume", "sheet", "differentiable", "rolling", "large", "batch", "serving", "cpu"}
+    sections = {"volume", "sheet", "differentiable", "rolling", "xshard", "large", "batch", "serving", "cpu"}
     only = sections if args.only == "all" else set() if args.only == "none" else set(args.only.split(","))
     if only - sections:
         ap.error(f"unknown sections {sorted(only - sections)}")
@@ -802,7 +838,8 @@ def main():
                    "raw": [cfg.nscan, cfg.nrows, cfg.ncols], "theta_deg": cfg.theta_deg,
                    "step_um": cfg.step, "pixel_um": cfg.pixel, "grid": [plan.nz, plan.ny, plan.nx],
                    "step": "fused deskew + z-MIP + y-MIP live view, one opm_project call, no volume in memory",
-                   "kernel_path": {"path": kname, "pixel_over_step": f"{path[1]}/{path[2]}" if path[1] else None},
+                   "kernel_path": {"path": kname, "pixel_over_step": f"{path[1]}/{path[2]}" if path[1] else None,
+                                   "unit_rows": opm.opm_plan_schedule(plan)[2]},
                    "l2": "input larger than L2 (raw 419 MB)",
                    "parallelism": f"{ws} independent stacks" if ws > 1 else "1 GPU"},
         "volumes_per_s": round(ws / (ms_step * 1e-3), 2),
@@ -841,6 +878,8 @@ def main():
         line["differentiable"] = adjoint_bench(torch, opm, peak, dshape)
     if "rolling" in only:
         line["rolling"] = rolling_bench(torch, opm, plan, host_raw, raw)
+    if "xshard" in only:
+        line["xshard"] = xshard_bench(torch, opm, cfg, raw, stream, ms_step * 1e-3)
     if "large" in only and not args.no_large:
         line["large_volume"] = large_bench(torch, opm, peak)
     if "batch" in only:

@@ -101,6 +101,19 @@ opm_status opm_plan_shape(const opm_plan* plan, int64_t* nz, int64_t* ny,
 typedef enum { OPM_PATH_GENERAL = 0, OPM_PATH_FAST = 1, OPM_PATH_PERIODIC = 2 } opm_path;
 opm_status opm_plan_path(const opm_plan* plan, int* path, int* fam_p, int* fam_q);
 
+/*
+ * opm_plan_schedule - the live-view schedule of the fast and periodic kernels
+ * (the live view of opm_project, Fig. 2d).  The work is cut into units of
+ * *chunk_rows camera rows of one 32-column j-tile at one 128-column x-tile,
+ * placed longest-first on *nlists lists, one per persistent CTA.  The plan
+ * takes the largest of 256, 128, 64, 32 and 16 rows that gives at least 1.1
+ * units per list, so that narrow stacks (an x-shard of one) still fill the
+ * GPU.  All three are 0 for a plan without that schedule (the general
+ * kernel's plans, and plans made with no CUDA device).  Any output pointer
+ * may be NULL.  Errors: OPM_ERR_INVALID_ARG (plan NULL).
+ */
+opm_status opm_plan_schedule(const opm_plan* plan, int64_t* nunits, int* nlists, int* chunk_rows);
+
 /* Frees a plan and its device tables.  NULL is accepted.  The caller must not
  * destroy a plan while work that uses it is still queued on a stream. */
 opm_status opm_plan_destroy(opm_plan* plan);

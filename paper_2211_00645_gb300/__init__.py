@@ -45,6 +45,8 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "opm_plan_shape": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4),
     "opm_plan_path": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3),
+    "opm_plan_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "opm_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "opm_deskew": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_void_p]),
@@ -178,6 +180,16 @@ def opm_plan_path(plan: Plan):
     v = [ctypes.c_int() for _ in range(3)]
     _check(load().opm_plan_path(plan.handle, *[ctypes.byref(x) for x in v]), "opm_plan_path")
     return tuple(x.value for x in v)
+
+
+def opm_plan_schedule(plan: Plan):
+    """``opm_plan_schedule``: (units, lists, rows per unit) of the plan's
+    live-view schedule; all 0 without one."""
+    n = ctypes.c_int64()
+    l, r = ctypes.c_int(), ctypes.c_int()
+    _check(load().opm_plan_schedule(plan.handle, ctypes.byref(n), ctypes.byref(l), ctypes.byref(r)),
+           "opm_plan_schedule")
+    return n.value, l.value, r.value
 
 
 def opm_plan_destroy(plan: Plan):

@@ -110,6 +110,7 @@ struct opm_plan {
   int fast_ok;        // full tiles never step more than one plane per column
   int family = 0;     // 1 + index into kFamilies when the periodic kernel applies, else 0
   int lists_per_sm = 4;  // persistent CTA lists per SM of the live-view schedule
+  int chunk_rows = 0;    // rows per work unit of that schedule (0: no schedule)
   std::vector<opm::Split> hA, hB;
   std::vector<opm::Band> hBand;
   std::vector<float> hYinit;

@@ -282,8 +282,14 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
     delete p;
     return cuda_fail(e, "cudaGetDevice");
   }
-  // The fast kernel's work units (x-tile, j-tile, chunk of kChunkRows rows of
-  // the tile's band) on balanced lists, one per persistent CTA.
+  // The fast kernel's work units (x-tile, j-tile, chunk of the tile's band)
+  // on balanced lists, one per persistent CTA.  A unit is a chain of ring
+  // stages that one CTA runs in order, so a plan with fewer units than lists
+  // runs for the length of its longest unit with most CTAs idle.  The chunk
+  // is the largest of kChunkRows, kChunkRows / 2, ..., kMinChunkRows rows that
+  // still gives every list at least kUnitsPerList units on average (larger
+  // chunks keep the DRAM locality of LPT's first round and pay the per-unit
+  // set-up and z-MIP fold fewer times).
   if (p->fast_ok) {
     int nsm = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -293,16 +299,25 @@ opm_status opm_plan_create(int64_t nscan, int64_t nrows, int64_t ncols,
     }
     try {
       const int xtiles = (int)((ncols + kUnitX - 1) / kUnitX);
+      const int nlists = std::min(std::max(nsm, 1) * p->lists_per_sm, kMaxLists);
+      auto nchunks = [&](int rows) {
+        int64_t n = 0;
+        for (const Band& bd : p->hBand)
+          if (bd.lo < bd.hi) n += (bd.hi - 1) / rows - bd.lo / rows + 1;
+        return n * xtiles;
+      };
+      int rows = kChunkRows;
+      while (rows > kMinChunkRows && (double)nchunks(rows) < kUnitsPerList * nlists) rows /= 2;
+      p->chunk_rows = rows;
       for (int jt = 0; jt < (int)p->hBand.size(); ++jt) {
         const Band bd = p->hBand[jt];
-        for (int c0 = (bd.lo / kChunkRows) * kChunkRows; c0 < bd.hi; c0 += kChunkRows) {
-          const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + kChunkRows);
+        for (int c0 = (bd.lo / rows) * rows; c0 < bd.hi; c0 += rows) {
+          const int ks = std::max(bd.lo, c0), ke = std::min(bd.hi, c0 + rows);
           if (ks >= ke) continue;
           for (int xt = 0; xt < xtiles; ++xt) p->hUnits.push_back(WorkUnit{0, xt, jt, ks, ke, 0, 0, 0});
         }
       }
       if (p->hUnits.size() > (size_t)INT32_MAX) p->fast_ok = 0;
-      const int nlists = std::min(std::max(nsm, 1) * p->lists_per_sm, kMaxLists);
       p->hLists.assign(nlists + 1, 0);
       schedule_lpt(p->hUnits.data(), (int)p->hUnits.size(), nlists, p->hLists.data());
     } catch (const std::bad_alloc&) {
@@ -396,6 +411,15 @@ opm_status opm_plan_path(const opm_plan* p, int* path, int* fam_p, int* fam_q) {
   if (path) *path = !fast ? OPM_PATH_GENERAL : p->family ? OPM_PATH_PERIODIC : OPM_PATH_FAST;
   if (fam_p) *fam_p = (fast && p->family) ? kFamilies[p->family - 1].p : 0;
   if (fam_q) *fam_q = (fast && p->family) ? kFamilies[p->family - 1].q : 0;
+  return OPM_OK;
+}
+
+opm_status opm_plan_schedule(const opm_plan* p, int64_t* nunits, int* nlists, int* chunk_rows) {
+  if (!p) return fail(OPM_ERR_INVALID_ARG, "plan is NULL");
+  const bool has = !p->hLists.empty();
+  if (nunits) *nunits = has ? (int64_t)p->hUnits.size() : 0;
+  if (nlists) *nlists = has ? (int)p->hLists.size() - 1 : 0;
+  if (chunk_rows) *chunk_rows = has ? p->chunk_rows : 0;
   return OPM_OK;
 }
 

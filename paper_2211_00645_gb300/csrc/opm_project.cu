@@ -33,10 +33,10 @@
 //                  host with the kernel's own arithmetic).  Two rows per stage
 //                  (one 3-input max per voxel pair into the z-max), packed
 //                  FP32x2 FMAs, one branch per column step, and each tile's
-//                  row band split into 256-row chunks whose z-maxima combine
-//                  by atomic max, which balances tiles of very different band
-//                  length; a persistent grid of 4 CTAs per SM walks the
-//                  chunks.
+//                  row band split into chunks (256 rows, fewer on narrow
+//                  stacks) whose z-maxima combine by atomic max, which
+//                  balances tiles of very different band length; a
+//                  persistent grid of 4 CTAs per SM walks the chunks.
 //  k_project_gen   every output (z-sum, first argmax), uint16 or FP32 input,
 //                  any tile (partial last tile, column steps of several
 //                  planes), one row per stage, whole band per CTA

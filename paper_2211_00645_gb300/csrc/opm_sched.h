@@ -19,9 +19,12 @@ struct __align__(16) WorkUnit {
 };
 static_assert(sizeof(WorkUnit) == 32, "WorkUnit is 32 bytes");
 
-// Rows per work unit of the single-stack fast projection, and columns x
-// per unit (one TMA box row of the fast kernels).
+// Largest and smallest rows per work unit of the single-stack fast
+// projection, the average units per CTA list the plan's choice between them
+// aims for, and columns x per unit (one TMA box row of the fast kernels).
 constexpr int kChunkRows = 256;
+constexpr int kMinChunkRows = 16;
+constexpr double kUnitsPerList = 1.1;
 constexpr int kUnitX = 128;
 
 // Upper bound on the number of CTA lists (4 CTAs per SM on up to 256 SMs).

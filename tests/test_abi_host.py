@@ -134,3 +134,11 @@ def test_plan_path_classification(opm):
         plan = opm.Plan(*shape)
         assert opm.opm_plan_path(plan) == want, shape
         plan.close()
+
+
+def test_plan_schedule_without_device(opm):
+    """A plan made with no CUDA device has no live-view schedule: units,
+    lists and rows per unit all read 0 (compute calls refuse such a plan)."""
+    plan = opm.Plan(200, 512, 2048, 35.0, 0.3, 0.1)
+    assert opm.opm_plan_schedule(plan) == (0, 0, 0)
+    plan.close()

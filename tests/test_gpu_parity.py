@@ -421,6 +421,32 @@ def test_liveview_full_size_every_column(lib, liveview):
     assert_close(out["ymip"].cpu().numpy(), ymip, what="ymip, every column")
 
 
+@pytest.mark.parametrize("width", [1024, 512, 256, 128])
+def test_liveview_narrow_stack_schedule(lib, liveview, width):
+    """The first `width` columns of the 200 x 512 x 2048 stack (an x-shard of
+    it): the plan cuts its units short enough that every persistent CTA list
+    still gets work (at least 1.1 units per list, or the 16-row floor), and
+    the live view matches the oracle on every column."""
+    from oracle_pool import project_columns
+    c, R = liveview
+    Rw = np.ascontiguousarray(R[:, :, :width])
+    plan = lib.Plan(c.nscan, c.nrows, width, c.theta_deg, c.step, c.pixel)
+    whole = lib.Plan(c.nscan, c.nrows, c.ncols, c.theta_deg, c.step, c.pixel)
+    nunits, nlists, rows = lib.opm_plan_schedule(plan)
+    _, wlists, wrows = lib.opm_plan_schedule(whole)
+    assert nlists == wlists > 0
+    assert rows in (16, 32, 64, 128, 256) and rows <= wrows
+    assert nunits >= 1.1 * nlists or rows == 16
+    if nlists <= 756:                       # 832 units of 256 rows at full width
+        assert wrows == 256
+    out = lib.project(plan, to_dev(Rw, torch), zmip=True, ymip=True)
+    torch.cuda.synchronize()
+    lib.opm_plan_check(plan)
+    zmip, ymip = project_columns(Rw, c.theta_deg, c.step, c.pixel)
+    assert_close(out["zmip"].cpu().numpy(), zmip, what=f"zmip, width {width}")
+    assert_close(out["ymip"].cpu().numpy(), ymip, what=f"ymip, width {width}")
+
+
 def test_large_full_size_sampled(lib):
     """1000 x 1024 x 2048 uint16 stack (theta 45, step 0.2, pixel 0.115):
     FP32 and round-to-nearest uint16 volumes and the z-MIP at full size,

@@ -301,10 +301,9 @@ def batch_bench(torch, opm, fixed=None):
     raw_b = sum(2 * k.numel() for k in keep)
     out = {"workload": "serving mix: 6 stacks, 2 channels each (theta 35, step 0.3, pixel 0.1), "
                        "z-MIP + y-MIP per channel, one batch", "items": len(items), "raw_bytes": raw_b}
-    if fixed:
-        shape, kchunk, ctas = fixed
+    def time_config(shape_id, kchunk, ctas):
         b = opm.Batch(max_items=len(items), max_units=1 << 24)
-        b.set(items, kchunk, SHAPE_IDS[shape])
+        b.set(items, kchunk, shape_id)
         b.upload()
         s = torch.cuda.current_stream()
         for _ in range(3):
@@ -315,9 +314,18 @@ def batch_bench(torch, opm, fixed=None):
             b.launch(ctas, s)
         e1.record(s)
         e1.synchronize()
-        out["fixed"] = {"shape": shape, "kchunk": kchunk, "ctas_per_sm": ctas,
-                        "us": round(e0.elapsed_time(e1) * 100, 2)}
+        b.check()
+        info = b.info()
+        return round(e0.elapsed_time(e1) * 100, 2), info
+
+    if fixed:
+        shape, kchunk, ctas = fixed
+        us, _ = time_config(SHAPE_IDS[shape], kchunk, ctas)
+        out["fixed"] = {"shape": shape, "kchunk": kchunk, "ctas_per_sm": ctas, "us": us}
     else:
+        # what a caller gets without the tuner: shape, kchunk and CTAs left at 0
+        us, info = time_config(opm.OPM_SHAPE_AUTO, 0, 0)
+        out["default"] = {"shape": opm.SHAPE_NAMES[info["shape"]], "units": info["units"], "us": us}
         e = Tuner().tune(items, reps=5, warmup=2)
         out["tuned"] = {k: e[k] for k in ("shape", "kchunk", "ctas_per_sm", "us")}
         out["candidates_us"] = e["candidates"]

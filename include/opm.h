@@ -333,7 +333,9 @@ typedef enum {
 /*
  * opm_batch_set - host-side preparation of the work list (TMA descriptors of
  * every item, unit lists sorted by decreasing length).  kchunk = rows per
- * unit of the fast kernels (0: 64); shape = an opm_shape (the one used is
+ * unit of the fast kernels (0: the largest of 256, 128, 64, 32 and 16 that
+ * gives at least 1.1 units per CTA list within max_units, as
+ * opm_plan_schedule describes); shape = an opm_shape (the one used is
  * reported by opm_batch_info).  Waits until the previous
  * opm_batch_upload of this batch has completed before overwriting its pinned
  * staging.  Every item's plan must live on the batch's device and stage at
@@ -406,7 +408,8 @@ opm_status opm_batch_destroy(opm_batch* b);
  * Limits: at most 64 items and 65536 work units per call (a unit is one
  * 32-column j-tile x 128-column x-tile x kchunk rows of one item); larger
  * requests fail with OPM_ERR_UNSUPPORTED and launch nothing.  Item rules as
- * for opm_batch_set.  kchunk: rows per unit (0: 64); ctas_per_sm: 1..4 (0: 4).
+ * for opm_batch_set.  kchunk: rows per unit (0: as opm_batch_set);
+ * ctas_per_sm: 1..4 (0: 4).
  * check != 0 synchronises cuda_stream afterwards and reports a failed
  * device consistency check as OPM_ERR_INTERNAL (a diagnostic, not for the
  * hot path).

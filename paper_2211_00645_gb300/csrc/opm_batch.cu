@@ -323,7 +323,8 @@ constexpr WorkList kEmptyWorkList = {kOffItems, 0, 0, 0, 0, 2, 0, 0, 2, kPerRun,
 //
 // An item goes to the fast kernels when its plan is fast-eligible and it
 // asks for z-MIP / y-MIP only (units: kchunk-row chunks of every tile's
-// band), else to the general kernel (units: whole bands; a tile with an
+// band; kchunk 0 takes the single-stack plan's rule over all fast items),
+// else to the general kernel (units: whole bands; a tile with an
 // empty band still gets a unit when the item has a z output, which the
 // unit's epilogue writes).  Zeroed outputs: every y-MIP and the z-MIP of
 // fast items (both combined by atomic max); the general kernel writes its
@@ -339,8 +340,28 @@ opm_status build_worklist(const opm_batch_item* items, int n_items, int kchunk, 
                                          std::to_string(max_items));
   if (!items && n_items > 0) return fail(OPM_ERR_INVALID_ARG, "items is NULL");
   if (kchunk < 0) return fail(OPM_ERR_INVALID_ARG, "kchunk must be >= 0");
-  if (kchunk == 0) kchunk = 64;
   if (!batch_encode_fn()) return fail(OPM_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is unavailable");
+  if (kchunk == 0) {
+    // The single-stack rule: the largest of kChunkRows .. kMinChunkRows rows
+    // that gives the CTA lists at least kUnitsPerList fast units each, without
+    // going past the unit capacity.  Items are validated by the pass below.
+    auto nfast_units = [&](int rows) {
+      int64_t n = 0;
+      for (int i = 0; i < n_items; ++i) {
+        const opm_batch_item& it = items[i];
+        const opm_plan* p = it.plan;
+        if (!p || gen_all || !plan_fast_ok(p) || it.zsum || it.argz || (!it.zmip && !it.ymip)) continue;
+        const int64_t xtiles = (p->nx + kX - 1) / kX;
+        for (const Band& bd : p->hBand)
+          if (bd.lo < bd.hi) n += xtiles * ((bd.hi - 1) / rows - bd.lo / rows + 1);
+      }
+      return n;
+    };
+    kchunk = kChunkRows;
+    while (kchunk > kMinChunkRows && (double)nfast_units(kchunk) < kUnitsPerList * nlists &&
+           nfast_units(kchunk / 2) <= max_units)
+      kchunk /= 2;
+  }
   const size_t off_segs = cal256(kOffItems + sizeof(BatchItemDev) * (size_t)n_items);
   const size_t off_lists = cal256(off_segs + sizeof(BatchSeg) * 2 * (size_t)n_items);
   const size_t off_glists = cal256(off_lists + sizeof(int) * (size_t)(nlists + 1));

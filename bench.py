@@ -54,14 +54,14 @@ KERNEL_SOURCES = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per full-size
 # launch from ncu captures, keyed by the hash of the kernel's sources at
 # capture time (reported as null once a source has changed).  periodic:
-# captured at full size (448.98 MB read, 9.33 MB written; 76.8 M warp
-# instructions from the full-size --set full capture).  volume_f32:
+# captured at full size (448.58 MB read, 9.17 MB written, 76.8 M warp
+# instructions).  volume_f32:
 # captured with 100 scan planes (213.11 MB read, 2963.51 MB written) and
 # scaled to 200 planes, reads by the raw bytes (x2.0) and writes by the
 # volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "periodic": {"src_sha": "7c739f76f346", "bytes_per_launch": 458307584, "warp_insts_per_launch": 76816260},
-    "volume_f32": {"src_sha": "1ea698c7952c", "bytes_per_launch": 4622836946},
+    "periodic": {"src_sha": "03f377e5e549", "bytes_per_launch": 457752064, "warp_insts_per_launch": 76816242},
+    "volume_f32": {"src_sha": "43cfe5fd23f6", "bytes_per_launch": 4622836946},
 }
 
 L2_BYTES = 129 * 10**6  # L2 of the GB300 (bytes)

@@ -368,6 +368,7 @@ def xshard_bench(torch, opm, cfg, raw, stream, t_whole):
                              "part_us": round(t * 1e6, 2), "copies": ncopy,
                              "efficiency": round(t_whole / (n * t), 3)}
         del part, parts, z, y
+    torch.cuda.empty_cache()
     return out
 
 

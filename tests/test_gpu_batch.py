@@ -312,3 +312,20 @@ def test_general_and_fast_items_nearest(lib):
         assert_between(it["ymip"].cpu().numpy(), lo.max(1), hi.max(1), what=f"ymip nearest {shape}")
         if "zsum" in keys:
             assert_between(it["zsum"].cpu().numpy(), lo.sum(0), hi.sum(0), what=f"zsum nearest {shape}")
+
+
+@pytest.mark.parametrize("width", [2048, 512, 128])
+def test_batch_default_units_follow_the_plan_rule(lib, width):
+    """kchunk 0: the batch cuts its fast items' units by the single-stack
+    plan's rule (largest of 256 .. 16 rows giving 1.1 units per CTA list), so
+    a batch of one stack holds exactly the plan's own units."""
+    plan = lib.Plan(200, 512, width, 35.0, 0.3, 0.1)
+    raw = torch.zeros(plan.raw_shape, dtype=torch.uint16, device="cuda")
+    z = torch.empty((plan.ny, plan.nx), device="cuda")
+    y = torch.empty((plan.nz, plan.nx), device="cuda")
+    nunits, nlists, rows = lib.opm_plan_schedule(plan)
+    assert nunits > 0 and nlists > 0 and rows in (16, 32, 64, 128, 256)
+    b = lib.Batch(max_items=1)
+    b.set([{"plan": plan, "raw": raw, "zmip": z, "ymip": y}])
+    assert b.info()["units"] == nunits
+    b.close()

@@ -210,6 +210,18 @@ opm_status opm_sheet_project(const void* raw, opm_dtype in_t, int64_t nscan, int
                              double shear, float* out, int64_t out_rows, void* cuda_stream);
 
 /*
+ * opm_sheet_check - uint16 stacks whose rows are a multiple of 8 columns
+ * (at least 128 columns, 33 rows, 16-byte aligned base) take a TMA kernel
+ * that stages each frame's rows through a ring with bounded waits; the
+ * others take a plain kernel.  A wait that gives up sets an error word on
+ * the device.  This call reads and clears the word of the current device:
+ * OPM_ERR_INTERNAL when a wait gave up since the last check (that view is
+ * incomplete), OPM_ERR_CUDA on a failed copy, else OPM_OK.  Synchronous
+ * (a blocking copy on the legacy default stream); not for the hot path.
+ */
+opm_status opm_sheet_check(void);
+
+/*
  * opm_warp_rows - the warp of the shear-warp view (Fig. 3): out[Y'][x] =
  * in at row a * Y' + b, linear between rows, zero outside [0, in_rows).
  * in [in_rows][ncols], out [out_rows][ncols], FP32 device arrays.

@@ -55,6 +55,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int64)]),
     "opm_sheet_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "opm_sheet_check": (ctypes.c_int, []),
     "opm_warp_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "opm_deskew_mip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
@@ -260,6 +261,12 @@ def opm_sheet_project(raw, shear: float, out=None, stream=None):
     _check(load().opm_sheet_project(_ptr(raw, None, "raw"), _dtype_code(raw), nscan, nrows, ncols, float(shear),
                                     _ptr(out, (H, ncols), "out"), H, _stream(stream)), "opm_sheet_project")
     return out
+
+
+def opm_sheet_check():
+    """``opm_sheet_check``: raises OpmError (OPM_ERR_INTERNAL) when a sheet-view
+    ring wait on the current device gave up since the last check."""
+    _check(load().opm_sheet_check(), "opm_sheet_check")
 
 
 def opm_warp_rows(inp, out_rows: int, a: float, b: float, out=None, stream=None):

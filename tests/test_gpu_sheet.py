@@ -32,6 +32,37 @@ def test_sheet_project_u16(lib, shape, shear):
         assert np.array_equal(out.cpu().numpy(), ref.astype(np.float32))
 
 
+@pytest.mark.parametrize("shape", [(120, 64, 136), (75, 40, 256), (60, 100, 128), (51, 33, 384)])
+@pytest.mark.parametrize("shear", [0.0, 1.0, 0.37, 2.4574561328, 7.5])
+def test_sheet_project_tma_path(lib, shape, shear):
+    """uint16 stacks the TMA kernel takes (rows of 8k columns, >= 128 columns,
+    >= 33 rows): a ragged last 128-column tile, output rows that are not a
+    multiple of the 32-row tile, several 50-frame chunks per tile, and frames
+    whose rows miss a tile.  Integer shears are exact; no ring wait gives up."""
+    R = _stack(*shape, seed=9)
+    out = lib.opm_sheet_project(to_dev(R, torch), shear)
+    torch.cuda.synchronize()
+    lib.opm_sheet_check()
+    ref = O.sheet_project(R.astype(np.float64), shear)
+    assert out.shape == ref.shape
+    assert_close(out.cpu().numpy(), ref, what=f"sheet tma {shape} shear={shear}")
+    if shear == math.floor(shear):
+        assert np.array_equal(out.cpu().numpy(), ref.astype(np.float32))
+
+
+def test_sheet_tma_and_plain_kernels_agree(lib):
+    """The same frames through the TMA kernel (136 columns) and the plain one
+    (a 130-column copy, not a multiple of 8): identical bits on the shared
+    columns."""
+    R = _stack(90, 48, 136, seed=4)
+    shear = 2.4574561328
+    a = lib.opm_sheet_project(to_dev(R, torch), shear)
+    b = lib.opm_sheet_project(to_dev(np.ascontiguousarray(R[:, :, :130]), torch), shear)
+    torch.cuda.synchronize()
+    lib.opm_sheet_check()
+    assert torch.equal(a[:, :130], b)
+
+
 def test_sheet_project_f32_signed(lib):
     R = opm_synth.gaussian((12, 20, 36), 4, np.float32)
     out = lib.opm_sheet_project(to_dev(R, torch), 1.3)

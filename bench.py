@@ -651,6 +651,7 @@ def sheet_bench(torch, opm, cfg, raw, stream, peak):
         opm.opm_sheet_project(raw, shear, out=sheet, stream=stream)
     s1.record(stream)
     torch.cuda.synchronize()
+    opm.opm_sheet_check()
     t_sheet = s0.elapsed_time(s1) / 20 * 1e-3
     sheet_b = 2 * cfg.nscan * cfg.nrows * cfg.ncols + 4 * sheet.numel()
     out = {"call": "opm_sheet_project", "shear_rows_per_frame": round(shear, 6),

@@ -112,7 +112,8 @@ k_sheet_project(const T* __restrict__ raw, int nscan, int nrows, int ncols, doub
 // kSY + 1 camera rows that the tile's rows interpolate between (one TMA box
 // {kSX, kSY + 1, 1}, zero-filled outside the frame) into a ring; four
 // compute warps (64 columns x 16 rows each, two columns per lane) convert
-// each staged row once and keep the running maxima in registers.  Chunks of
+// each staged row once and keep the running maxima in registers, taking
+// two frames per step (one 3-input max per voxel and frame pair).  Chunks of
 // one tile combine by atomic max into the zeroed output (uint16 views are
 // >= 0, so integer order is float order).  Frames whose rows miss the tile
 // entirely are skipped: they contribute 0, which the zeroed output holds.
@@ -121,9 +122,9 @@ k_sheet_project(const T* __restrict__ raw, int nscan, int nrows, int ncols, doub
 constexpr int kSY = 32;                       // output rows per tile
 constexpr int kSRows = kSY + 1;               // camera rows staged per frame
 constexpr int kSX = 128;                      // columns per tile (TMA box width)
-constexpr int kSStages = 6;                   // ring depth
 constexpr int kSCW = 4;                       // compute warps
 constexpr int kSHalf = kSY / 2;               // output rows per compute warp
+constexpr int kSStages = 6;                   // ring depth
 constexpr int kSChunk = 50;                   // frames per CTA, at most
 constexpr unsigned kSStageBytes = kSRows * kSX * 2;
 static_assert(kSStageBytes % 128 == 0, "ring stages stay 128-byte aligned");
@@ -195,9 +196,49 @@ k_sheet_tma(const __grid_constant__ CUtensorMap map, int nscan, int nrows, int n
   float m[kSHalf][2];
 #pragma unroll
   for (int t = 0; t < kSHalf; ++t) m[t][0] = m[t][1] = 0.0f;
+  int n = n0;
 #pragma unroll 1
-  for (int n = n0; n < n1; ++n) {
-    if (!feeds(n)) continue;
+  while (true) {
+    while (n < n1 && !feeds(n)) ++n;
+    if (n >= n1) break;
+    // two frames at a time (one 3-input max per voxel pair), a single one last
+    int nb = n + 1;
+    while (nb < n1 && !feeds(nb)) ++nb;
+    if (nb < n1) {
+      const int s = g % kSStages, s2 = (g + 1) % kSStages;
+      if (!mbar_wait(&full[s], (g / kSStages) & 1, err) || !mbar_wait(&full[s2], ((g + 1) / kSStages) & 1, err)) {
+        ok = false;
+        break;
+      }
+      const ShiftSplit sp = shift[n - n0], sq = shift[nb - n0];
+      const float w = sp.f > 0.0f ? 1.0f - sp.f : 0.0f;
+      const float w2 = sq.f > 0.0f ? 1.0f - sq.f : 0.0f;
+      const f2 ww = pk(w, w), ww2 = pk(w2, w2);
+      const unsigned char* row = ssm + (size_t)s * kSStageBytes + (size_t)t0 * (kSX * 2) + xl * 2;
+      const unsigned char* row2 = ssm + (size_t)s2 * kSStageBytes + (size_t)t0 * (kSX * 2) + xl * 2;
+      f2 a = u16x2_to_f2(*reinterpret_cast<const uint32_t*>(row));
+      f2 a2 = u16x2_to_f2(*reinterpret_cast<const uint32_t*>(row2));
+#pragma unroll
+      for (int t = 0; t < kSHalf; ++t) {
+        const f2 b = u16x2_to_f2(*reinterpret_cast<const uint32_t*>(row + (t + 1) * (kSX * 2)));
+        const f2 b2 = u16x2_to_f2(*reinterpret_cast<const uint32_t*>(row2 + (t + 1) * (kSX * 2)));
+        float v0, v1, u0, u1;
+        upk(fma2(ww, sub2(b, a), a), v0, v1);
+        upk(fma2(ww2, sub2(b2, a2), a2), u0, u1);
+        m[t][0] = max3(m[t][0], v0, u0);
+        m[t][1] = max3(m[t][1], v1, u1);
+        a = b;
+        a2 = b2;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&sfree[s]);
+        mbar_arrive(&sfree[s2]);
+      }
+      g += 2;
+      n = nb + 1;
+      continue;
+    }
     const int s = g % kSStages;
     if (!mbar_wait(&full[s], (g / kSStages) & 1, err)) {
       ok = false;
@@ -220,6 +261,7 @@ k_sheet_tma(const __grid_constant__ CUtensorMap map, int nscan, int nrows, int n
     __syncwarp();
     if (lane == 0) mbar_arrive(&sfree[s]);
     ++g;
+    ++n;
   }
   if (!ok) return;
   const int x = x0 + xl;

@@ -139,6 +139,20 @@ def test_plan_path_classification(opm):
 def test_plan_schedule_without_device(opm):
     """A plan made with no CUDA device has no live-view schedule: units,
     lists and rows per unit all read 0 (compute calls refuse such a plan)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only behaviour needs a machine without a CUDA device")
     plan = opm.Plan(200, 512, 2048, 35.0, 0.3, 0.1)
     assert opm.opm_plan_schedule(plan) == (0, 0, 0)
     plan.close()
+
+
+def test_sheet_check_without_device(opm):
+    """With no usable CUDA device the sheet view's error-word check reports
+    OPM_ERR_CUDA rather than failing silently or crashing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only behaviour needs a machine without a CUDA device")
+    with pytest.raises(opm.OpmError) as e:
+        opm.opm_sheet_check()
+    assert e.value.status == opm.OPM_ERR_CUDA

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "opm_tma.cuh"
@@ -277,9 +278,8 @@ k_sheet_tma(const __grid_constant__ CUtensorMap map, int nscan, int nrows, int n
 
 PFN_cuTensorMapEncodeTiled_v12000 sheet_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
@@ -288,7 +288,7 @@ PFN_cuTensorMapEncodeTiled_v12000 sheet_encode_fn() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     else
       cudaGetLastError();
-  }
+  });
   return fn;
 }
 
@@ -327,20 +327,28 @@ k_warp_rows(const float* __restrict__ in, int H, int ncols, float* __restrict__ 
 
 // The TMA form: uint16 stacks with rows of a multiple of 8 columns (16-byte
 // strides), a 16-byte aligned base, and at least one full box of rows and
-// columns.  Returns false (nothing launched) when it does not apply.
+// columns.  Sets *launched = false (nothing launched) when it does not apply.
 opm_status launch_sheet_tma(const void* raw, int nscan, int nrows, int ncols, double shear, float* out, int H,
                             int dev, cudaStream_t s, bool* launched) {
   *launched = false;
   if (ncols % 8 != 0 || (uintptr_t)raw % 16 != 0 || nrows < kSRows || ncols < kSX || !sheet_encode_fn())
     return OPM_OK;
-  static int attr_done[64] = {0};
+  // per-device set-up, once: the shared-memory limit and the address of the
+  // device's error word (taken under the lock, so no launch sees a null one)
+  static std::mutex mu;
   static unsigned* err_ptr[64] = {nullptr};
+  unsigned* err = nullptr;
   cudaError_t e;
-  if (!attr_done[dev]) {
-    e = cudaFuncSetAttribute(k_sheet_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sheet_tma_smem());
-    if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err_ptr[dev]), g_sheet_err);
-    if (e != cudaSuccess) return cuda_fail(e, "set-up of k_sheet_tma");
-    attr_done[dev] = 1;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!err_ptr[dev]) {
+      unsigned* p = nullptr;
+      e = cudaFuncSetAttribute(k_sheet_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sheet_tma_smem());
+      if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_sheet_err);
+      if (e != cudaSuccess) return cuda_fail(e, "set-up of k_sheet_tma");
+      err_ptr[dev] = p;
+    }
+    err = err_ptr[dev];
   }
   CUtensorMap map;
   const cuuint64_t dims[3] = {(cuuint64_t)ncols, (cuuint64_t)nrows, (cuuint64_t)nscan};
@@ -358,8 +366,7 @@ opm_status launch_sheet_tma(const void* raw, int nscan, int nrows, int ncols, do
   if (grid.y > 65535 || grid.z > 65535) return fail(OPM_ERR_UNSUPPORTED, "too many output rows or frames");
   e = cudaMemsetAsync(out, 0, sizeof(float) * (size_t)H * (size_t)ncols, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (sheet view)");
-  k_sheet_tma<<<grid, 32 * (kSCW + 1), sheet_tma_smem(), s>>>(map, nscan, nrows, ncols, shear, out, H, chunk,
-                                                              err_ptr[dev]);
+  k_sheet_tma<<<grid, 32 * (kSCW + 1), sheet_tma_smem(), s>>>(map, nscan, nrows, ncols, shear, out, H, chunk, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "launch k_sheet_tma");
   *launched = true;

@@ -256,6 +256,42 @@ opm_status opm_warp_rows(const float* in, int64_t in_rows, int64_t ncols, float*
  * OPM_ERR_CUDA.
  */
 opm_status opm_stream_begin(const opm_plan* plan, float* zmip, float* zsum, float* ymip, void* cuda_stream);
+
+/*
+ * opm_max_combine - out[i] = max(a[i], b[i]) for i < n, FP32 device arrays
+ * (out may be a or b).  The maximum over frames is associative and exact, so
+ * the projections of disjoint sets of plane pairs (each accumulated by
+ * opm_stream_pair from zeroed outputs) combine to the projection of their
+ * union bit for bit; the sliding view of a camera stream (Fig. 4a, a full
+ * stack of the newest frames) keeps such partial maxima and combines them
+ * per frame.  Asynchronous on cuda_stream; allocates nothing.
+ * Errors: OPM_ERR_INVALID_ARG (NULL array, n < 0), OPM_ERR_CUDA.
+ */
+opm_status opm_max_combine(float* out, const float* a, const float* b, int64_t n, void* cuda_stream);
+
+/*
+ * opm_sliding_push - the sliding live view (Fig. 4a refreshed after every
+ * frame, always spanning a full stack of the newest frames): call it after
+ * writing frame m (0 <= m < nscan) of the current stack into stack[m]
+ * ([nscan][nrows][ncols] uint16, device), on the stream that wrote it.
+ * Frames 0..m are then the current stack's and m+1..nscan-1 the previous
+ * stack's (all zero before the first).  Each projection buffer is an FP32
+ * z-MIP [ny][nx] followed by a y-MIP [nz][nx] (P = ny nx + nz nx floats):
+ *   run   [P]         maximum over the current stack's complete plane pairs;
+ *   slots [nscan][P]  slot q: the previous stack's maximum over its pairs
+ *                     q..nscan-1, until the current stack's pair q replaces
+ *                     it (slot 0 is not used);
+ *   view  [P]         the published projections.
+ * All three must be zero before the first push and are owned by the caller.
+ * After the call, view equals opm_project of the stack buffer bit for bit
+ * (z-MIP and y-MIP).  A call costs two opm_stream_pair passes, one zeroing
+ * and two maxima over P; the call for m = nscan - 1 also builds the next
+ * suffixes (nscan - 2 maxima).  Asynchronous; allocates nothing.
+ * Errors: OPM_ERR_INVALID_ARG (NULL, m out of range), OPM_ERR_UNSUPPORTED
+ * (more than 65535 rows), OPM_ERR_CUDA.
+ */
+opm_status opm_sliding_push(const opm_plan* plan, const uint16_t* stack, int64_t m, float* run, float* slots,
+                            float* view, void* cuda_stream);
 opm_status opm_stream_pair(const opm_plan* plan, const uint16_t* plane_lo, const uint16_t* plane_hi, int64_t n,
                            float* zmip, float* zsum, float* ymip, void* cuda_stream);
 

@@ -56,6 +56,8 @@ _SIGS = {
     "opm_sheet_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "opm_sheet_check": (ctypes.c_int, []),
+    "opm_max_combine": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_void_p]),
+    "opm_sliding_push": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 4),
     "opm_warp_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "opm_deskew_mip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
@@ -261,6 +263,30 @@ def opm_sheet_project(raw, shear: float, out=None, stream=None):
     _check(load().opm_sheet_project(_ptr(raw, None, "raw"), _dtype_code(raw), nscan, nrows, ncols, float(shear),
                                     _ptr(out, (H, ncols), "out"), H, _stream(stream)), "opm_sheet_project")
     return out
+
+
+def opm_max_combine(out, a, b, stream=None):
+    """``opm_max_combine``: out = max(a, b) elementwise (float32 CUDA tensors of
+    one shape; out may be a or b)."""
+    torch = _torch()
+    for t, name in ((out, "out"), (a, "a"), (b, "b")):
+        if t.dtype != torch.float32:
+            raise TypeError(f"{name} must be float32")
+    n = out.numel()
+    if a.numel() != n or b.numel() != n:
+        raise ValueError("out, a and b must hold the same number of values")
+    _check(load().opm_max_combine(_ptr(out, None, "out"), _ptr(a, None, "a"), _ptr(b, None, "b"), n,
+                                  _stream(stream)), "opm_max_combine")
+    return out
+
+
+def opm_sliding_push(plan: Plan, stack, m: int, run, slots, view, stream=None):
+    """``opm_sliding_push`` on CUDA tensors: stack uint16 [nscan][nrows][ncols],
+    run and view float32 [P], slots float32 [nscan][P], P = ny nx + nz nx."""
+    P = plan.ny * plan.nx + plan.nz * plan.nx
+    _check(load().opm_sliding_push(plan.handle, _ptr(stack, plan.raw_shape, "stack"), int(m),
+                                   _ptr(run, (P,), "run"), _ptr(slots, (plan.nscan, P), "slots"),
+                                   _ptr(view, (P,), "view"), _stream(stream)), "opm_sliding_push")
 
 
 def opm_sheet_check():

@@ -155,6 +155,8 @@ opm_status launch_warp_rows(const float* in, int H, int ncols, float* out, int H
 opm_status launch_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, cudaStream_t s);
 opm_status launch_stream_pair(const opm_plan* p, const uint16_t* lo, const uint16_t* hi, int n, float* zmip,
                               float* zsum, float* ymip, cudaStream_t s);
+opm_status launch_sliding_push(const opm_plan* p, const uint16_t* stack, int m, float* run, float* slots,
+                               float* view, cudaStream_t s);
 opm_status launch_adjoint(const opm_plan* p, const void* vol, void* raw_out,
                           opm_dtype t, cudaStream_t s);
 opm_status launch_mip_backward(const opm_plan* p, const float* g,

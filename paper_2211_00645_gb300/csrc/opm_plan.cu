@@ -509,6 +509,15 @@ opm_status opm_stream_pair(const opm_plan* p, const uint16_t* plane_lo, const ui
   return launch_stream_pair(p, plane_lo, plane_hi, (int)n, zmip, zsum, ymip, static_cast<cudaStream_t>(stream));
 }
 
+opm_status opm_sliding_push(const opm_plan* p, const uint16_t* stack, int64_t m, float* run, float* slots,
+                            float* view, void* stream) {
+  opm_status st = check_plan(p);
+  if (st != OPM_OK) return st;
+  if (!stack || !run || !slots || !view) return fail(OPM_ERR_INVALID_ARG, "stack, run, slots and view must be non-NULL");
+  if (m < 0 || m > p->nscan - 1) return fail(OPM_ERR_INVALID_ARG, "m must lie in [0, nscan - 1]");
+  return launch_sliding_push(p, stack, (int)m, run, slots, view, static_cast<cudaStream_t>(stream));
+}
+
 opm_status opm_deskew_dual(const opm_plan* p, const void* raw, opm_dtype in_t, float* vol_f32,
                            uint16_t* vol_u16, void* stream) {
   opm_status st = check_plan(p);

@@ -6,6 +6,8 @@
 // plane, so the calls for n = -1 .. nscan - 1 cover the volume once; the
 // per-voxel arithmetic (plane, weight, FMA on the plane difference) is the
 // fast projection's, so the z-MIP and y-MIP end bit-identical to it.
+#include <algorithm>
+
 #include "opm_common.cuh"
 
 namespace opm {
@@ -114,6 +116,26 @@ k_stream_pair(PlanView v, const uint16_t* __restrict__ lo, const uint16_t* __res
   }
 }
 
+// out[i] = max(a[i], b[i]) over n FP32 values (out may alias a or b):
+// the combine of the sliding view's partial projections.  Four values per
+// thread when all three arrays are 16-byte aligned and n is a multiple of 4.
+__global__ void __launch_bounds__(256)
+k_max_combine(float* out, const float* a, const float* b, long long n, int vec) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    const long long n4 = n / 4;
+    for (; i < n4; i += stride) {
+      const float4 x = reinterpret_cast<const float4*>(a)[i];
+      const float4 y = reinterpret_cast<const float4*>(b)[i];
+      reinterpret_cast<float4*>(out)[i] =
+          make_float4(fmaxf(x.x, y.x), fmaxf(x.y, y.y), fmaxf(x.z, y.z), fmaxf(x.w, y.w));
+    }
+  } else {
+    for (; i < n; i += stride) out[i] = fmaxf(a[i], b[i]);
+  }
+}
+
 }  // namespace
 
 opm_status launch_stream_begin(const opm_plan* p, float* zmip, float* zsum, float* ymip, cudaStream_t s) {
@@ -135,3 +157,77 @@ opm_status launch_stream_pair(const opm_plan* p, const uint16_t* lo, const uint1
 }
 
 }  // namespace opm
+
+namespace opm {
+namespace {
+
+opm_status launch_max_combine(float* out, const float* a, const float* b, int64_t n, cudaStream_t s) {
+  if (n == 0) return OPM_OK;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device query (max combine)");
+  const int vec = (n % 4 == 0) && ((uintptr_t)out % 16 == 0) && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0);
+  const long long work = vec ? n / 4 : n;
+  const long long blocks = std::min<long long>((work + 255) / 256, (long long)std::max(nsm, 1) * 8);
+  k_max_combine<<<(unsigned)blocks, 256, 0, s>>>(out, a, b, (long long)n, vec);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_max_combine");
+}
+
+}  // namespace
+
+// The sliding view after frame m of the current stack has been written to
+// stack[m] (frames 0..m new, m+1..nscan-1 the previous stack's).  Each
+// projection buffer is one z-MIP [ny][nx] followed by one y-MIP [nz][nx];
+// `run` holds the maximum of the new stack's complete pairs, slot q of
+// `slots` the previous stack's suffix maximum over its pairs q..nscan-1
+// until the new stack's pair q replaces it.  The maximum is associative and
+// exact, so `view` ends equal to the projection of the whole buffer.
+opm_status launch_sliding_push(const opm_plan* p, const uint16_t* stack, int m, float* run, float* slots,
+                               float* view, cudaStream_t s) {
+  const PlanView& v = p->view;
+  const int N = v.nscan;
+  const size_t zn = (size_t)v.ny * v.nx, per = zn + (size_t)v.nz * v.nx;
+  const size_t frame = (size_t)v.nrows * v.ncols;
+  auto F = [&](int n) { return stack + (size_t)n * frame; };
+  auto slot = [&](int q) { return slots + (size_t)q * per; };
+  opm_status st = OPM_OK;
+  // pair q (frames q, q + 1 of the new stack) into slot q, then into run
+  auto pair_into_slot = [&](int q) {
+    float* b = slot(q);
+    opm_status r = launch_stream_begin(p, b, nullptr, b + zn, s);
+    if (r == OPM_OK) r = launch_stream_pair(p, F(q), q + 1 < N ? F(q + 1) : nullptr, q, b, nullptr, b + zn, s);
+    if (r == OPM_OK) r = launch_max_combine(run, run, b, (int64_t)per, s);
+    return r;
+  };
+  if (m == 0) {  // pair -1: the new stack's first frame alone
+    st = launch_stream_begin(p, run, nullptr, run + zn, s);
+    if (st == OPM_OK) st = launch_stream_pair(p, nullptr, F(0), -1, run, nullptr, run + zn, s);
+  } else if (m == 1) {  // pair 0 is never read from a slot: straight into run
+    st = launch_stream_pair(p, F(0), F(1), 0, run, nullptr, run + zn, s);
+  } else {
+    st = pair_into_slot(m - 1);
+  }
+  if (st != OPM_OK) return st;
+  if (m == N - 1) {  // the last frame closes the stack, then the next suffixes
+    st = pair_into_slot(N - 1);
+    if (st == OPM_OK) st = launch_max_combine(view, run, run, (int64_t)per, s);
+    for (int q = N - 2; q >= 1 && st == OPM_OK; --q) st = launch_max_combine(slot(q), slot(q), slot(q + 1), (int64_t)per, s);
+    return st;
+  }
+  // new pairs, the previous stack's pairs m + 1 .. N - 1, then the mixed pair m
+  st = launch_max_combine(view, run, slot(m + 1), (int64_t)per, s);
+  if (st == OPM_OK) st = launch_stream_pair(p, F(m), F(m + 1), m, view, nullptr, view + zn, s);
+  return st;
+}
+
+}  // namespace opm
+
+using namespace opm;
+
+extern "C" opm_status opm_max_combine(float* out, const float* a, const float* b, int64_t n, void* stream) {
+  if (!out || !a || !b) return fail(OPM_ERR_INVALID_ARG, "out, a and b must be non-NULL");
+  if (n < 0) return fail(OPM_ERR_INVALID_ARG, "n must be >= 0");
+  return launch_max_combine(out, a, b, n, static_cast<cudaStream_t>(stream));
+}

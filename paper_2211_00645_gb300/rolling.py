@@ -11,16 +11,29 @@ far; in global mode only the push that completes a stack does.
 
 A third mode, sliding, keeps the latest frame of every scan position in a
 device stack buffer (frame n of the current stack replaces frame n of the
-previous one) and re-projects the whole buffer after every frame with the
-fused projection, so the view always spans a full stack: the newest frames
+previous one), so the view always spans a full stack: the newest frames
 where they exist, the previous stack's elsewhere (zeros before the first
-stack completes).
+stack completes).  After new frame m the view is the projection of pairs
+-1 .. m - 1 (new frames only), pair m (new frame m, old frame m + 1) and
+pairs m + 1 .. nscan - 1 (old frames only).  The maximum is associative
+and exact, so the view is kept as three parts:
+  * R, the running maximum of the new stack's complete pairs;
+  * slot p, the previous stack's suffix maximum over its pairs p ..
+    nscan - 1 (built in one pass when that stack completed), until the new
+    stack's pair p overwrites it with its own partial projection;
+  * the mixed pair m, folded into the view directly.
+One opm_sliding_push call per frame does it in the library: two pair
+passes, one zeroing and two elementwise maxima instead of a whole
+re-projection, and the view equals opm_project of the mixed stack bit for
+bit.  The completing frame also builds the next suffixes (nscan - 2
+maxima).  With a z-sum the mode re-projects the buffer after every frame
+instead (sums would change their rounding order).
 """
 from __future__ import annotations
 
 from typing import Optional
 
-from . import Plan, opm_stream_begin, opm_stream_pair
+from . import Plan, opm_sliding_push, opm_stream_begin, opm_stream_pair
 
 
 class RollingView:
@@ -40,8 +53,19 @@ class RollingView:
             self.frames = []
         else:
             self.frames = [torch.empty((plan.nrows, plan.ncols), dtype=torch.uint16, device=dev) for _ in range(2)]
-        self.zmip = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
-        self.ymip = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
+        zn, P = plan.ny * plan.nx, plan.ny * plan.nx + plan.nz * plan.nx
+        self.fast_sliding = mode == "sliding" and not zsum
+        if self.fast_sliding:
+            # opm_sliding_push's buffers, each a z-MIP followed by a y-MIP, all
+            # zero at first (the projection of the all-zero stack)
+            self.run = torch.zeros(P, dtype=torch.float32, device=dev)
+            self.slots = torch.zeros((plan.nscan, P), dtype=torch.float32, device=dev)
+            self.view = torch.zeros(P, dtype=torch.float32, device=dev)
+            self.zmip = self.view[:zn].view(plan.ny, plan.nx)
+            self.ymip = self.view[zn:].view(plan.nz, plan.nx)
+        else:
+            self.zmip = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
+            self.ymip = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
         self.zsum = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev) if zsum else None
         self.n = 0            # frames of the current stack received so far
         self.stacks = 0       # completed stacks
@@ -82,12 +106,16 @@ class RollingView:
         return None
 
     def _push_sliding(self, frame) -> dict:
-        from . import opm_project
         torch = self.torch
         p = self.plan
+        m = self.n
         with torch.cuda.stream(self.stream):
-            self.stack[self.n].view(torch.int16).copy_(frame.view(torch.int16), non_blocking=True)
-        opm_project(p, self.stack, self.zmip, self.zsum, self.ymip, None, self.stream)
+            self.stack[m].view(torch.int16).copy_(frame.view(torch.int16), non_blocking=True)
+        if self.fast_sliding:
+            opm_sliding_push(p, self.stack, m, self.run, self.slots, self.view, self.stream)
+        else:
+            from . import opm_project
+            opm_project(p, self.stack, self.zmip, self.zsum, self.ymip, None, self.stream)
         self.n += 1
         complete = self.n == p.nscan
         if complete:

@@ -151,3 +151,49 @@ def test_sliding_mode_spans_a_full_stack(lib):
     assert torch.equal(out["zmip"], ref["zmip"]) and torch.equal(out["ymip"], ref["ymip"])
     zr, _, yr, _ = O.project(mixed.astype(np.float64), O.geometry(*shape))
     assert_close(out["zmip"].cpu().numpy(), zr, what="sliding zmip")
+
+
+@pytest.mark.parametrize("shape", [(12, 40, 72, 35.0, 0.3, 0.1), (2, 30, 64, 35.0, 0.3, 0.1),
+                                   (9, 20, 64, 35.0, 0.05, 0.1), (7, 9, 30, 90.0, 0.1, 0.1)])
+def test_sliding_view_every_push_over_three_stacks(lib, shape):
+    """Sliding mode (running maximum + the previous stack's suffix maxima +
+    the mixed pair): after every push of three stacks, starting from the
+    all-zero stack, the view equals opm_project of the stack buffer it spans
+    (newest frames 0..m, the previous stack's m+1..N-1) bit for bit."""
+    from paper_2211_00645_gb300.rolling import RollingView
+    plan = lib.Plan(*shape)
+    N = plan.nscan
+    stacks = [_stack(shape, seed=40 + i) for i in range(3)]
+    view = RollingView(plan, mode="sliding")
+    buf = np.zeros_like(stacks[0])
+    for si, S in enumerate(stacks):
+        hs = torch.from_numpy(S.view(np.int16)).view(torch.uint16)
+        for m in range(N):
+            out = view.push(hs[m])
+            buf[m] = S[m]
+            torch.cuda.synchronize()
+            ref = lib.project(plan, to_dev(buf, torch), zmip=True, ymip=True)
+            assert out["complete"] == (m == N - 1)
+            assert torch.equal(out["zmip"], ref["zmip"]), (si, m, "zmip")
+            assert torch.equal(out["ymip"], ref["ymip"]), (si, m, "ymip")
+        assert out["stacks"] == si + 1
+    lib.opm_plan_check(plan)
+
+
+def test_max_combine(lib):
+    """opm_max_combine: elementwise maximum, in place or into a third array,
+    on aligned (vector) and unaligned / ragged (scalar) arrays, with signed
+    values and infinities."""
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for n, off in ((4096, 0), (1001, 0), (4096, 1)):
+        a = torch.randn(n + off, device="cuda", generator=g)[off:]
+        b = torch.randn(n + off, device="cuda", generator=g)[off:]
+        a[::7] = -float("inf")
+        out = torch.empty(n, device="cuda")
+        lib.opm_max_combine(out, a, b)
+        torch.cuda.synchronize()
+        assert torch.equal(out, torch.maximum(a, b))
+        a2 = a.clone()
+        lib.opm_max_combine(a2, a2, b)
+        torch.cuda.synchronize()
+        assert torch.equal(a2, torch.maximum(a, b))

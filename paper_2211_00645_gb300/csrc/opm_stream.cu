@@ -15,7 +15,9 @@ namespace opm {
 namespace {
 
 constexpr int kSVec = 4;         // columns x per thread
-constexpr int kSThreads = 128;   // threads per CTA, along x
+constexpr int kSLanesX = 32;     // threads along x (one warp): 128 columns per CTA
+constexpr int kSRowsCta = 8;     // camera rows per CTA, one warp each
+constexpr int kSTileJ = 32;      // columns j of the CTA's shared z-MIP tile
 constexpr int kSearchSteps = 64; // bound on the column search of one row
 
 __global__ void k_stream_zero(float* zmip, float* zsum, long long nj, float* ymip, long long nk) {
@@ -49,70 +51,103 @@ __device__ __forceinline__ void load_row(const uint16_t* __restrict__ plane, con
   }
 }
 
-// One CTA row per camera row k (blockIdx.y), kSThreads x kSVec columns per
-// CTA.  The columns j of row k whose lower plane is n form one run; it is
-// found from an FP32 estimate and corrected with the exact split-table
-// arithmetic.
-__global__ void __launch_bounds__(kSThreads)
+// A CTA covers kSRowsCta consecutive camera rows (one warp each, blockIdx.y)
+// and kSLanesX x kSVec columns x (blockIdx.x).  The columns j of row k whose
+// lower plane is n form one run; it is found from an FP32 estimate and
+// corrected with the exact split-table arithmetic.  The runs move up in j
+// with k (n0 grows with j and falls with k), so the CTA's rows share a
+// narrow band of columns j: their z-MIP values meet in a shared tile of
+// kSTileJ columns from the first row's run start (shared atomic max), and
+// the tile goes to the global z-MIP once per (j, x) at the end.  Voxels past
+// the tile take the global atomic directly.  uint16 voxels are >= 0 and the
+// outputs start at 0, so a zero left in the tile is skipped: the maxima are
+// the same bits as one global atomic per voxel.
+__global__ void __launch_bounds__(kSLanesX * kSRowsCta)
 k_stream_pair(PlanView v, const uint16_t* __restrict__ lo, const uint16_t* __restrict__ hi, int n, float* zmip,
               float* zsum, float* ymip, int vec_ok) {
-  const int k = blockIdx.y;
-  const int x0 = (blockIdx.x * kSThreads + threadIdx.x) * kSVec;
-  if (x0 >= v.nx) return;
-  const Split b = v.B[k];
+  __shared__ float zt[kSTileJ][kSLanesX * kSVec];
+  __shared__ int jbase_s;
+  const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
+  const int k = blockIdx.y * kSRowsCta + wrow;
+  const int xl = lane * kSVec;
+  const int x0 = blockIdx.x * (kSLanesX * kSVec) + xl;
+  for (int i = threadIdx.x; i < kSTileJ * kSLanesX * kSVec; i += blockDim.x) (&zt[0][0])[i] = 0.0f;
   // first column with lower plane >= n: estimate, then walk (bounded)
-  const float half = v.linear ? 0.0f : 0.5f;
-  const float est = (float)v.J0 + ((float)n - half + (float)b.i + b.f) * v.rinv;
-  int j = (int)fminf(fmaxf(floorf(est), 0.0f), (float)(v.ny - 1));
-  int n0;
-  float w;
-  int steps = 0;
-  while (j > 0 && steps < kSearchSteps) {
-    plane_weight(v.A[j - 1], b, v.linear, n0, w);
-    if (n0 < n) break;
-    --j;
-    ++steps;
-  }
-  while (j < v.ny && steps < kSearchSteps) {
-    plane_weight(v.A[j], b, v.linear, n0, w);
-    if (n0 >= n) break;
-    ++j;
-    ++steps;
-  }
-  if (steps >= kSearchSteps) {
-    if (threadIdx.x == 0) atomicOr(v.err, kErrSearch);
-    return;
-  }
-  float a[kSVec], d[kSVec];
-  const bool vec = vec_ok && x0 + kSVec <= v.nx;
-  load_row(lo, v, k, x0, vec, a);
-  load_row(hi, v, k, x0, vec, d);
-#pragma unroll
-  for (int i = 0; i < kSVec; ++i) d[i] = d[i] - a[i];  // exact: integers below 2^24
-  float ym[kSVec];
-#pragma unroll
-  for (int i = 0; i < kSVec; ++i) ym[i] = 0.0f;  // uint16 voxels are >= 0
-  bool any = false;
-#pragma unroll 1
-  for (; j < v.ny; ++j) {
-    plane_weight(v.A[j], b, v.linear, n0, w);
-    if (n0 != n) break;
-    any = true;
-    const size_t row = (size_t)j * v.nx + x0;
-#pragma unroll
-    for (int i = 0; i < kSVec; ++i) {
-      if (x0 + i >= v.nx) break;
-      const float val = fmaf(w, d[i], a[i]);
-      ym[i] = fmaxf(ym[i], val);
-      if (zmip) atomicMax(reinterpret_cast<int*>(zmip + row + i), __float_as_int(val));
-      if (zsum) atomicAdd(zsum + row + i, val);
+  int j = 0, n0 = 0, steps = 0;
+  float w = 0.0f;
+  const bool row_ok = k < v.nz;
+  Split b{0, 0.0f};
+  if (row_ok) {
+    b = v.B[k];
+    const float half = v.linear ? 0.0f : 0.5f;
+    const float est = (float)v.J0 + ((float)n - half + (float)b.i + b.f) * v.rinv;
+    j = (int)fminf(fmaxf(floorf(est), 0.0f), (float)(v.ny - 1));
+    while (j > 0 && steps < kSearchSteps) {
+      plane_weight(v.A[j - 1], b, v.linear, n0, w);
+      if (n0 < n) break;
+      --j;
+      ++steps;
+    }
+    while (j < v.ny && steps < kSearchSteps) {
+      plane_weight(v.A[j], b, v.linear, n0, w);
+      if (n0 >= n) break;
+      ++j;
+      ++steps;
     }
   }
-  if (ymip && any) {
-    float* yr = ymip + (size_t)k * v.nx + x0;
+  const bool found = row_ok && steps < kSearchSteps;
+  if (row_ok && !found && lane == 0) atomicOr(v.err, kErrSearch);
+  if (wrow == 0) jbase_s = j;  // the first row's run start (row 0 of a CTA always exists)
+  __syncthreads();
+  const int jbase = jbase_s;
+  if (found && x0 < v.nx) {
+    float a[kSVec], d[kSVec];
+    const bool vec = vec_ok && x0 + kSVec <= v.nx;
+    load_row(lo, v, k, x0, vec, a);
+    load_row(hi, v, k, x0, vec, d);
 #pragma unroll
-    for (int i = 0; i < kSVec; ++i)
-      if (x0 + i < v.nx) yr[i] = fmaxf(yr[i], ym[i]);  // one thread per (k, x) in this launch
+    for (int i = 0; i < kSVec; ++i) d[i] = d[i] - a[i];  // exact: integers below 2^24
+    float ym[kSVec];
+#pragma unroll
+    for (int i = 0; i < kSVec; ++i) ym[i] = 0.0f;  // uint16 voxels are >= 0
+    bool any = false;
+#pragma unroll 1
+    for (; j < v.ny; ++j) {
+      plane_weight(v.A[j], b, v.linear, n0, w);
+      if (n0 != n) break;
+      any = true;
+      const int jt = j - jbase;  // >= 0: runs move up with k
+      const bool in_tile = jt >= 0 && jt < kSTileJ;
+      const size_t row = (size_t)j * v.nx + x0;
+#pragma unroll
+      for (int i = 0; i < kSVec; ++i) {
+        if (x0 + i >= v.nx) break;
+        const float val = fmaf(w, d[i], a[i]);
+        ym[i] = fmaxf(ym[i], val);
+        if (zmip) {
+          if (in_tile)
+            atomicMax(reinterpret_cast<int*>(&zt[jt][xl + i]), __float_as_int(val));
+          else
+            atomicMax(reinterpret_cast<int*>(zmip + row + i), __float_as_int(val));
+        }
+        if (zsum) atomicAdd(zsum + row + i, val);
+      }
+    }
+    if (ymip && any) {
+      float* yr = ymip + (size_t)k * v.nx + x0;
+#pragma unroll
+      for (int i = 0; i < kSVec; ++i)
+        if (x0 + i < v.nx) yr[i] = fmaxf(yr[i], ym[i]);  // one thread per (k, x) in this launch
+    }
+  }
+  if (!zmip) return;
+  __syncthreads();
+  const int xb = blockIdx.x * (kSLanesX * kSVec);
+  for (int i = threadIdx.x; i < kSTileJ * kSLanesX * kSVec; i += blockDim.x) {
+    const int jt = i / (kSLanesX * kSVec), xx = i % (kSLanesX * kSVec);
+    const float val = (&zt[0][0])[i];
+    if (val != 0.0f && jbase + jt < v.ny && xb + xx < v.nx)
+      atomicMax(reinterpret_cast<int*>(zmip + (size_t)(jbase + jt) * v.nx + xb + xx), __float_as_int(val));
   }
 }
 
@@ -148,10 +183,11 @@ opm_status launch_stream_begin(const opm_plan* p, float* zmip, float* zsum, floa
 opm_status launch_stream_pair(const opm_plan* p, const uint16_t* lo, const uint16_t* hi, int n, float* zmip,
                               float* zsum, float* ymip, cudaStream_t s) {
   const PlanView& v = p->view;
-  const int xblocks = (v.nx + kSThreads * kSVec - 1) / (kSThreads * kSVec);
+  const int xblocks = (v.nx + kSLanesX * kSVec - 1) / (kSLanesX * kSVec);
   if (v.nz > 65535) return fail(OPM_ERR_UNSUPPORTED, "more than 65535 camera rows");
   const int vec_ok = (v.ncols % kSVec == 0) && ((uintptr_t)lo % 8 == 0) && ((uintptr_t)hi % 8 == 0);
-  k_stream_pair<<<dim3(xblocks, v.nz), kSThreads, 0, s>>>(v, lo, hi, n, zmip, zsum, ymip, vec_ok);
+  const int rblocks = (v.nz + kSRowsCta - 1) / kSRowsCta;
+  k_stream_pair<<<dim3(xblocks, rblocks), kSLanesX * kSRowsCta, 0, s>>>(v, lo, hi, n, zmip, zsum, ymip, vec_ok);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OPM_OK : cuda_fail(e, "launch k_stream_pair");
 }

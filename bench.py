@@ -60,8 +60,8 @@ KERNEL_SOURCES = {
 # scaled to 200 planes, reads by the raw bytes (x2.0) and writes by the
 # volume bytes (x1.4161).
 NCU_TRAFFIC = {
-    "periodic": {"src_sha": "83f674096cd3", "bytes_per_launch": 457752064, "warp_insts_per_launch": 76816242},
-    "volume_f32": {"src_sha": "4e97167a55d3", "bytes_per_launch": 4622836946},
+    "periodic": {"src_sha": "0916abe0e7ee", "bytes_per_launch": 457752064, "warp_insts_per_launch": 76816242},
+    "volume_f32": {"src_sha": "4eff36766d3d", "bytes_per_launch": 4622836946},
 }
 
 L2_BYTES = 129 * 10**6  # L2 of the GB300 (bytes)

@@ -756,7 +756,7 @@ def main():
     zmip = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
     ymip = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
     # the FP32 volume only for the volume section (the step never writes one)
-    vol = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev) if "volume" in only else None
+    vol = None  # the FP32 volume: allocated for the volume section, after serving
     host_z = torch.empty((plan.ny, plan.nx), dtype=torch.float32).pin_memory()
     host_y = torch.empty((plan.nz, plan.nx), dtype=torch.float32).pin_memory()
     stream = torch.cuda.current_stream()
@@ -792,23 +792,6 @@ def main():
     ms_step = pdist.max_over_ranks(total_ms / K, device=dev)
     opm.opm_plan_check(plan)
 
-    # ---- the separate full FP32 volume run of the same stack: the volume alone,
-    # and volume + live view from one opm_deskew_mip call (side by side)
-    t_vol = t_pair = None
-    if vol is not None:
-        KV = max(20, K // 8)
-        v0, v1, v2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        v0.record(stream)
-        for _ in range(KV):
-            opm.opm_deskew(plan, raw, vol, stream)
-        v1.record(stream)
-        for _ in range(KV):
-            opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
-        v2.record(stream)
-        torch.cuda.synchronize()
-        t_vol = v0.elapsed_time(v1) / KV * 1e-3
-        t_pair = v1.elapsed_time(v2) / KV * 1e-3
-        opm.opm_plan_check(plan)
     opm.opm_plan_check(plan)
 
     # ---- end to end through the C ABI: every step copies its stack in from
@@ -897,6 +880,34 @@ def main():
         "host": {"cores": os.cpu_count(), "library_sources_sha": _tree_sha()},
         "clocks": clocks,
     }
+    # Serving runs first among the sections, right after the step: its host
+    # threads and copies were slowed by what ran before it in the process
+    # (sections that allocate and free GB of device buffers), while serving
+    # alone after the step measured cleanly.  The stack stays where the step
+    # allocated it for the sections after serving.
+    if "serving" in only:
+        torch.cuda.empty_cache()
+        line["serving"] = serve_bench(args, torch)
+    # ---- the separate full FP32 volume run of the same stack: the volume alone,
+    # and volume + live view from one opm_deskew_mip call (side by side)
+    if "volume" in only:
+        vol = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            opm.opm_deskew(plan, raw, vol, stream)
+            opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+        KV = max(20, K // 8)
+        v0, v1, v2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        v0.record(stream)
+        for _ in range(KV):
+            opm.opm_deskew(plan, raw, vol, stream)
+        v1.record(stream)
+        for _ in range(KV):
+            opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
+        v2.record(stream)
+        torch.cuda.synchronize()
+        t_vol = v0.elapsed_time(v1) / KV * 1e-3
+        t_pair = v1.elapsed_time(v2) / KV * 1e-3
+        opm.opm_plan_check(plan)
     vtr = NCU_TRAFFIC.get("volume_f32")
     if vol is not None:
         line["volume"] = {
@@ -911,6 +922,8 @@ def main():
                                         "frac": round(pair_b / t_pair / 1e9 / peak, 4)},
             "one_pass_fused": one_pass(torch, opm, cfg, raw, vol, zmip, ymip, stream, vol_b, live_b, peak),
         }
+        vol = None
+        torch.cuda.empty_cache()
     if "sheet" in only:
         line["sheet_view"] = sheet_bench(torch, opm, cfg, raw, stream, peak)
     if "differentiable" in only:
@@ -923,18 +936,8 @@ def main():
     if "batch" in only:
         bc = args.batch_config.split(",") if args.batch_config else None
         line["batch"] = batch_bench(torch, opm, (bc[0], int(bc[1]), int(bc[2])) if bc else None)
-    if "serving" in only:
-        vol = raw = None
-        torch.cuda.empty_cache()
-        line["serving"] = serve_bench(args, torch)
-    # after serving: the section's many medium device allocations, made just
-    # before it, slowed the serving loop's copies and ticks in the same process
     if "xshard" in only:
-        if raw is None:
-            raw = torch.empty(plan.raw_shape, dtype=torch.uint16, device=dev)
-            raw.view(torch.int16).copy_(host_raw)
         line["xshard"] = xshard_bench(torch, opm, cfg, raw, stream, ms_step * 1e-3)
-        raw = None
     if "cpu" in only and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(R, cfg, args.ref_cols)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(R, cfg)

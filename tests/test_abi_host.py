@@ -156,3 +156,20 @@ def test_sheet_check_without_device(opm):
     with pytest.raises(opm.OpmError) as e:
         opm.opm_sheet_check()
     assert e.value.status == opm.OPM_ERR_CUDA
+
+
+def test_sliding_and_combine_argument_checks(opm):
+    """opm_max_combine and opm_sliding_push refuse bad arguments before any
+    device work: NULL arrays, a negative length, a NULL plan, a frame index
+    outside [0, nscan)."""
+    lib = opm.load()
+    p = ctypes.c_void_p(16)
+    assert lib.opm_max_combine(None, p, p, 4, None) == opm.OPM_ERR_INVALID_ARG
+    assert lib.opm_max_combine(p, p, p, -1, None) == opm.OPM_ERR_INVALID_ARG
+    assert lib.opm_sliding_push(None, p, 0, p, p, p, None) == opm.OPM_ERR_INVALID_ARG
+    import torch
+    if not torch.cuda.is_available():
+        plan = opm.Plan(8, 6, 16, 30.0, 0.4, 0.115)
+        # a plan made without a device refuses before looking at the arguments
+        assert lib.opm_sliding_push(plan.handle, p, 0, p, p, p, None) == opm.OPM_ERR_CUDA
+        plan.close()

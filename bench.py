@@ -755,8 +755,7 @@ def main():
     raw.view(torch.int16).copy_(host_raw)
     zmip = torch.empty((plan.ny, plan.nx), dtype=torch.float32, device=dev)
     ymip = torch.empty((plan.nz, plan.nx), dtype=torch.float32, device=dev)
-    # the FP32 volume only for the volume section (the step never writes one)
-    vol = None  # the FP32 volume: allocated for the volume section, after serving
+    vol = None  # the FP32 volume: allocated for the volume section, after serving (the step never writes one)
     host_z = torch.empty((plan.ny, plan.nx), dtype=torch.float32).pin_memory()
     host_y = torch.empty((plan.nz, plan.nx), dtype=torch.float32).pin_memory()
     stream = torch.cuda.current_stream()
@@ -767,9 +766,6 @@ def main():
 
     for _ in range(args.warmup):
         step()
-        if vol is not None:
-            opm.opm_deskew(plan, raw, vol, stream)
-            opm.opm_deskew_mip(plan, raw, vol, None, zmip, ymip, stream)
     torch.cuda.synchronize()
     opm.opm_plan_check(plan)
 
